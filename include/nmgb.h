@@ -1,0 +1,164 @@
+/*
+ * nmgb.h -- C ABI of the GB300 (sm_103a) library for the nodal finite-difference effective field and
+ * Landau-Lifshitz-Gilbert integration of NeuralMag (Abert et al., arXiv 2411.11725).
+ *
+ * Model (section, equation labels of the paper):
+ *   - Magnetisation m is a nodal vector field on a regular grid of N1 x N2 x N3 cuboid cells of size
+ *     dx1 x dx2 x dx3 ("Nodal Finite-Difference Scheme", multi-indices c, n, i; Eq. nodal_basis).
+ *   - Material parameters Ms, A, Ku are cell-wise constants (Eqs. ms_discrete, cell_basis).  A cell
+ *     with Ms = 0 is vacuum and contributes to no term.
+ *   - The effective field (Eq. heff) is the sum of exchange (Eq. exchange_energy), uniaxial
+ *     anisotropy E = -int Ku (m.e)^2, Zeeman E = -mu0 int Ms h.m, each from its weak form (Eq.
+ *     weak_form_discrete) assembled cell by cell (Eqs. weak_form_impl_f, weak_form_impl) and divided
+ *     by the lumped nodal mass (Eq. mass_lumping); and the demagnetising field of homogeneously
+ *     magnetised cuboid cells by zero-padded FFT convolution with node->cell and cell->node averaging
+ *     (section "Demagnetization Field").  mu0 = 4 pi 1e-7.
+ *   - LLG right-hand side: Eq. llg.  Integrators: classical RK4 and adaptive Dormand-Prince 5(4)
+ *     (section "Automatic Differentiation and Time Integration").
+ *
+ * Layouts at this boundary (C order, component fastest, as the paper's tensors):
+ *   nodal vector field  (N1+1, N2+1, N3+1, 3)
+ *   cell scalar         (N1, N2, N3)
+ *   cell vector         (N1, N2, N3, 3)
+ *
+ * Precision: NM_F32 evaluates h_eff (stencils, FFT demag, LLG right-hand side) in FP32 and keeps the
+ * magnetisation, the RK error norm, step control and the Newell tensor set-up in FP64.  NM_F64 does
+ * everything in FP64.  "real" below means float for NM_F32 meshes and double for NM_F64 meshes.
+ *
+ * Ownership: the caller owns every pointer it passes and may reuse it once the call returns (host
+ * pointers) or once the mesh's stream has passed the call (device pointers).  The library owns the
+ * mesh and its device workspaces.  Work is enqueued on the mesh's CUDA stream; calls that return host
+ * values synchronise that stream.
+ *
+ * Errors: every entry point returns NM_OK (0) or a negative NM_ERR_* code and leaves a message for
+ * nm_last_error() (thread-local).  No C++ exception crosses this boundary.  Arguments are validated
+ * on the host before anything is enqueued.
+ */
+#ifndef NMGB_H
+#define NMGB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NM_OK 0
+#define NM_ERR_ARG (-1)             /* invalid argument: shape, null pointer, non-positive size ... */
+#define NM_ERR_OOM (-2)             /* device memory allocation failed */
+#define NM_ERR_CUDA (-3)            /* a CUDA runtime call failed */
+#define NM_ERR_STEP_UNDERFLOW (-4)  /* adaptive step size fell below dt_min or too many rejections */
+#define NM_ERR_NONFINITE (-5)       /* non-finite values met where finite ones are required */
+#define NM_ERR_TIMEOUT (-6)         /* a bounded wait ran out */
+#define NM_ERR_STATE (-7)           /* call out of order, e.g. stepping before a state was set */
+
+#define NM_F32 0  /* FP32 field evaluation, FP64 state and step control */
+#define NM_F64 1  /* FP64 throughout */
+
+/* effective-field terms (bit mask) */
+#define NM_EXCH 1u
+#define NM_ANIS 2u
+#define NM_ZEE 4u
+#define NM_DEMAG 8u
+#define NM_ALL 15u
+
+/* integrators */
+#define NM_RK4 1   /* classical Runge-Kutta, fixed step */
+#define NM_DP54 2  /* Dormand-Prince 5(4), FSAL, adaptive */
+
+/* nm_set_field kinds */
+#define NM_FIELD_HEXT_UNIFORM 1  /* uniform applied field (A/m) */
+#define NM_FIELD_HEXT_CELL 2     /* cell-wise applied field (A/m), cell vector layout */
+
+/* memory spaces of state pointers */
+#define NM_MEM_HOST 0
+#define NM_MEM_DEVICE 1
+
+typedef struct nm_mesh_s *nm_mesh;
+
+/* Create a mesh of n1 x n2 x n3 cells of size dx1 x dx2 x dx3 (metres), precision NM_F32 or NM_F64,
+ * working on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
+ * Allocates every device workspace the mesh needs.  Errors: NM_ERR_ARG (n_k < 1, dx_k <= 0, bad
+ * precision, out == NULL), NM_ERR_OOM, NM_ERR_CUDA. */
+int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision,
+                   void *cuda_stream, nm_mesh *out);
+
+/* Release a mesh and all its device memory (synchronises its stream).  NULL is accepted. */
+int nm_destroy_mesh(nm_mesh mesh);
+
+/* Material (Eqs. ms_discrete, cell_basis): host FP64 cell scalars Ms (A/m), A (J/m), Ku (J/m^3); a
+ * NULL array means the uniform value Ms0 / A0 / Ku0.  axis: host double[3], the uniaxial easy axis
+ * (normalised here; must be non-zero).  alpha: Gilbert damping; gamma: reduced gyromagnetic ratio in
+ * m/(A s) (Eq. llg).  Builds the lumped nodal mass (Eq. mass_lumping) and, on first call, the demag
+ * tensor spectrum.  Errors: NM_ERR_ARG (negative Ms, zero axis, non-finite values), NM_ERR_CUDA. */
+int nm_set_material(nm_mesh mesh, const double *Ms, double Ms0, const double *A, double A0,
+                    const double *Ku, double Ku0, const double axis[3], double alpha, double gamma);
+
+/* Applied field for the Zeeman term.  kind NM_FIELD_HEXT_UNIFORM: h(t) = amp * s(t), data ignored.
+ * kind NM_FIELD_HEXT_CELL: h_c(t) = data_c * s(t) with data a host FP64 cell vector field (NULL
+ * removes the cell field), amp ignored.  s(t) = 1 for freq_hz == 0, else sin(2 pi freq_hz t + phase).
+ * The two kinds add up.  Errors: NM_ERR_ARG. */
+int nm_set_field(nm_mesh mesh, int kind, const double *data, const double amp[3], double freq_hz,
+                 double phase);
+
+/* Resident state for the integrators: m (FP64 nodal vector field, host or device pointer per
+ * `where`), time t, next step size dt.  Invalidates the FSAL slope. Errors: NM_ERR_ARG. */
+int nm_set_state(nm_mesh mesh, const double *m, int where, double t, double dt);
+
+/* Copy the resident state out: m_out (FP64 nodal vector field, host or device per `where`; may be
+ * NULL), t and dt (may be NULL).  Synchronises the stream. */
+int nm_get_state(nm_mesh mesh, double *m_out, int where, double *t, double *dt);
+
+/* Integrator options: renormalise |m| = 1 after each accepted step (default 1); smallest allowed
+ * adaptive step dt_min (default 1e-22 s); consecutive rejections before NM_ERR_STEP_UNDERFLOW
+ * (default 50). */
+int nm_set_integrator(nm_mesh mesh, int renormalise, double dt_min, int max_rejections);
+
+/* Effective field h = H_eff(m) at time t for the terms in the mask (NM_EXCH|NM_ANIS|NM_ZEE|NM_DEMAG):
+ * m and h_out are DEVICE pointers to real nodal vector fields; m == NULL uses the resident state.
+ * Nodes that touch no magnetic cell get h = 0.  Asynchronous.  Errors: NM_ERR_ARG, NM_ERR_STATE
+ * (material not set), NM_ERR_CUDA. */
+int nm_h_eff(nm_mesh mesh, const void *m, void *h_out, unsigned terms, double t);
+
+/* Select the field terms used by the integrators (default NM_ALL). */
+int nm_set_terms(nm_mesh mesh, unsigned terms);
+
+/* One integrator step on the resident state.  NM_RK4 uses *dt as the fixed step; NM_DP54 attempts
+ * *dt and on return *dt holds the proposed next step, *accepted tells whether the attempt was taken
+ * (error norm <= 1 with tolerances rtol, atol).  *t is advanced on acceptance.  Synchronises.
+ * Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_STEP_UNDERFLOW, NM_ERR_CUDA. */
+int nm_llg_step(nm_mesh mesh, int method, double *t, double *dt, double rtol, double atol, int *accepted);
+
+/* n_steps step attempts with no host round trip in between (step control runs on the device; the
+ * step is replayed from a captured CUDA graph).  The resident t and dt are used and advanced.
+ * Asynchronous: read results with nm_get_state or nm_get_counters. */
+int nm_run_steps(nm_mesh mesh, int method, long n_steps, double rtol, double atol);
+
+/* Accepted/rejected step counters and the last error norm (synchronises). Pointers may be NULL. */
+int nm_get_counters(nm_mesh mesh, long *n_accepted, long *n_rejected, double *last_err);
+
+/* Integrate the resident state to t_end.  NM_RK4 uses the fixed step dt0 (the last step is
+ * shortened to land on t_end); NM_DP54 starts from dt0 (or the resident dt when dt0 <= 0).  When
+ * sample_dt > 0, step ends are clipped to the sample times t0 + k sample_dt and the volume-weighted
+ * mean of m (weights: lumped nodal volume) is written to samples_out[k*3 + j] (host FP64 array of
+ * max_samples x 3) for k = 0 .. while t0 + k sample_dt <= t_end (k = 0 is the initial state).
+ * n_accepted / n_rejected may be NULL.  Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_STEP_UNDERFLOW,
+ * NM_ERR_CUDA. */
+int nm_run_until(nm_mesh mesh, double t_end, int method, double rtol, double atol, double dt0,
+                 double sample_dt, double *samples_out, long max_samples, long *n_accepted,
+                 long *n_rejected);
+
+/* Sizes of the mesh: nodes, cells, padded FFT lengths P1 P2 P3, and the device bytes the mesh holds. */
+int nm_mesh_info(nm_mesh mesh, long *n_nodes, long *n_cells, int P[3], long *device_bytes);
+
+/* Device bytes a mesh of this shape and precision would hold (for admission by HBM footprint). */
+long nm_footprint_bytes(int n1, int n2, int n3, int precision);
+
+/* Block until all work enqueued on the mesh's stream has finished. */
+int nm_sync(nm_mesh mesh);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *nm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NMGB_H */

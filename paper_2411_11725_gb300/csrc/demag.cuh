@@ -1,0 +1,47 @@
+// Demagnetising field by zero-padded FFT convolution on the cell grid with node->cell and
+// cell->node averaging (section "Demagnetization Field" of the paper).  The padded transform is
+// never materialised: every pass reads only the non-zero part of its input and writes only the part
+// of its output that later passes use.
+#pragma once
+#include "nm_common.cuh"
+
+namespace nm {
+
+struct Geom {
+    int N1, N2, N3;            // cells
+    int nn1, nn2, nn3;         // nodes = cells + 1
+    long n_nodes, n_cells;
+    long ns;                   // component stride of nodal SoA arrays
+    long cs;                   // component stride of cell SoA arrays
+    int P1, P2, P3;            // padded FFT lengths (1 when N_k == 1)
+    int Q, lgQ, lgP2, lgP3;    // Q = P1/2 (complex length of the x transform), 0 when P1 == 1
+    int X, Xp;                 // X = P1/2 + 1 half-spectrum length, Xp = X padded for grouping
+    int H2, H3;                // tensor octant lengths P2/2+1, P3/2+1
+    int twlg;                  // log2 of the twiddle table length
+    long s_comp;               // component stride of the spectrum buffer = N3 * P2 * Xp
+    long t_comp;               // component stride of the tensor spectrum = H3 * H2 * Xp
+};
+
+template <typename T>
+struct DemagBufs {
+    Cx<T> *S;                  // spectra [3][N3][P2][Xp]
+    const T *Nk;               // tensor spectrum [6][H3][H2][Xp], already scaled by -1/(P1 P2 P3)
+    const Cx<T> *tw;           // twiddle table e^{-2 pi i k / 2^twlg}
+    const T *Ms;               // cell Ms map (SoA, n_cells) or NULL for uniform
+    T Ms0;
+    const StepCtl *ctl;        // when set, passes do nothing once ctl->done (finished integrations)
+};
+
+// Demag of the nodal field y (SoA, real T): writes (Ms_c H_c) per cell into MsH (3 x cs).
+template <typename T>
+void demag_forward(const Geom &g, const DemagBufs<T> &b, const T *y, T *MsH, cudaStream_t st);
+
+// Same pipeline with an explicit cell input: M (3 x cs, already Ms-weighted cell magnetisation)
+// replaces the node->cell averaging; output H (3 x cs) without the Ms factor.  Used by the adjoint.
+template <typename T>
+void demag_cells(const Geom &g, const DemagBufs<T> &b, const T *M, T *H, cudaStream_t st);
+
+// Raise the dynamic shared-memory limit of every demag kernel once (outside any graph capture).
+void demag_init_attributes();
+
+}  // namespace nm

@@ -1,0 +1,393 @@
+// Runge-Kutta bookkeeping kernels: stage inputs, Dormand-Prince error norm with a deterministic
+// two-level reduction, device-side step control, the accepted update with renormalisation, and the
+// boundary layout conversions.
+#include "rk.cuh"
+
+namespace nm {
+
+constexpr int kRedThreads = 256;
+
+// y = m + dt * sum_j a_j k_j   (FP64 accumulation; y in the working precision)
+template <typename T>
+__global__ void k_stage_input(long n_nodes, long ns, const double *__restrict__ m, KList k, const StepCtl *ctl,
+                              T *__restrict__ y)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    if (ctl->done) return;
+    const double dt = ctl->dt;
+    for (int c = 0; c < 3; ++c) {
+        long i = c * ns + n;
+        double acc = 0.0;
+        for (int j = 0; j < k.n; ++j) acc += k.a[j] * (double)((const T *)k.p[j])[i];
+        y[i] = (T)(m[i] + dt * acc);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// Per-block partial sums of ((dt sum_i e_i k_i) / (atol + rtol max(|m|, |m5|)))^2 over magnetic
+// nodes, m5 = m + dt sum_i b_i k_i.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, const double *__restrict__ m,
+                                                          KList kb, KList ke, const T *__restrict__ inv_mass,
+                                                          const StepCtl *ctl, double *partials)
+{
+    __shared__ double sh[kRedThreads];
+    if (ctl->done) return;
+    const double dt = ctl->dt, rtol = ctl->rtol, atol = ctl->atol;
+    double acc = 0.0;
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < n_nodes; n += (long)gridDim.x * blockDim.x) {
+        if (!(inv_mass[n] > T(0))) continue;
+        for (int c = 0; c < 3; ++c) {
+            long i = c * ns + n;
+            double sb = 0.0, se = 0.0;
+            for (int j = 0; j < kb.n; ++j) {
+                double kv = (double)((const T *)kb.p[j])[i];
+                sb += kb.a[j] * kv;
+                se += ke.a[j] * kv;
+            }
+            double m0 = m[i], m5 = m0 + dt * sb;
+            double sc = atol + rtol * fmax(fabs(m0), fabs(m5));
+            double q = dt * se / sc;
+            acc += q * q;
+        }
+    }
+    double s = block_sum<T>(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// One block: err = sqrt(sum partials / (3 n_active)); accept when err <= 1; new dt from
+// dt * clamp(0.9 err^(-1/5), 0.2, 5); clipping to t_end; failure after too many rejections.
+__global__ void __launch_bounds__(1024) k_dp5_ctl(const double *partials, int nparts, double n_active, StepCtl *ctl,
+                                                  int max_rej)
+{
+    __shared__ double sh[1024];
+    if (ctl->done) {
+        if (threadIdx.x == 0) ctl->accepted = 0;
+        return;
+    }
+    double v = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += partials[i];
+    double s = block_sum<double>(v, sh);
+    if (threadIdx.x != 0) return;
+    double err = n_active > 0 ? sqrt(s / (3.0 * n_active)) : 0.0;
+    bool fin = isfinite(err);
+    bool acc = fin && err <= 1.0;
+    double fac = !fin ? 0.2 : (err == 0.0 ? 5.0 : fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2))));
+    ctl->err = err;
+    ctl->accepted = acc;
+    ctl->dt_used = ctl->dt;
+    if (acc) {
+        ctl->t += ctl->dt;
+        ctl->n_acc += 1;
+        ctl->consecutive_rej = 0;
+    } else {
+        ctl->n_rej += 1;
+        ctl->consecutive_rej += 1;
+    }
+    double dtn = ctl->dt * fac;
+    ctl->dt_prop = dtn;
+    if (ctl->t_end > 0.0) {
+        double rem = ctl->t_end - ctl->t;
+        if (rem <= 1e-12 * fmax(fabs(ctl->t_end), 1e-30)) {
+            ctl->done = 1;
+        } else if (dtn > rem) {
+            dtn = rem;
+        }
+    }
+    if (ctl->consecutive_rej > max_rej || (!ctl->done && dtn < ctl->dt_min)) {
+        ctl->status = NM_ERR_STEP_UNDERFLOW;
+        ctl->done = 1;
+    }
+    ctl->dt = dtn;
+}
+
+// Accepted step: m <- m5 (optionally renormalised), k1 <- k7 (FSAL).  Rejected: nothing.
+template <typename T>
+__global__ void k_dp5_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const T *__restrict__ k7,
+                             T *__restrict__ k1, const StepCtl *ctl, int renorm)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    if (!ctl->accepted) return;
+    const double dt = ctl->dt_used;
+    double v[3];
+    for (int c = 0; c < 3; ++c) {
+        long i = c * ns + n;
+        double sb = 0.0;
+        for (int j = 0; j < kb.n; ++j) sb += kb.a[j] * (double)((const T *)kb.p[j])[i];
+        v[c] = m[i] + dt * sb;
+    }
+    if (renorm) {
+        double s = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (s > 0.0) { v[0] /= s; v[1] /= s; v[2] /= s; }
+    }
+    for (int c = 0; c < 3; ++c) {
+        long i = c * ns + n;
+        m[i] = v[c];
+        k1[i] = k7[i];
+    }
+}
+
+// RK4 end of step: m <- m + dt/6 (k1 + 2 k2 + 2 k3 + k4), optional renormalisation.
+template <typename T>
+__global__ void k_rk4_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const StepCtl *ctl, int renorm)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    if (ctl->done) return;
+    const double dt = ctl->dt;
+    double v[3];
+    for (int c = 0; c < 3; ++c) {
+        long i = c * ns + n;
+        double sb = 0.0;
+        for (int j = 0; j < kb.n; ++j) sb += kb.a[j] * (double)((const T *)kb.p[j])[i];
+        v[c] = m[i] + dt * sb;
+    }
+    if (renorm) {
+        double s = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        if (s > 0.0) { v[0] /= s; v[1] /= s; v[2] /= s; }
+    }
+    for (int c = 0; c < 3; ++c) m[c * ns + n] = v[c];
+}
+
+__global__ void k_rk4_advance(StepCtl *ctl)
+{
+    if (ctl->done) return;
+    ctl->t += ctl->dt;
+    ctl->n_acc += 1;
+    ctl->accepted = 1;
+    ctl->dt_used = ctl->dt;
+    if (ctl->t_end > 0.0) {
+        double rem = ctl->t_end - ctl->t;
+        if (rem <= 1e-12 * fmax(fabs(ctl->t_end), 1e-30)) ctl->done = 1;
+        else if (ctl->dt > rem) ctl->dt = rem;
+    }
+}
+
+// Volume-weighted mean of m: per-block partial sums of (w m_x, w m_y, w m_z, w).
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) k_mean_partials(long n_nodes, long ns, const double *__restrict__ m,
+                                                                const T *__restrict__ vol, double *partials)
+{
+    __shared__ double sh[kRedThreads];
+    double a[4] = {0, 0, 0, 0};
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < n_nodes; n += (long)gridDim.x * blockDim.x) {
+        double w = (double)vol[n];
+        a[0] += w * m[n];
+        a[1] += w * m[ns + n];
+        a[2] += w * m[2 * ns + n];
+        a[3] += w;
+    }
+    for (int c = 0; c < 4; ++c) {
+        double s = block_sum<T>(a[c], sh);
+        if (threadIdx.x == 0) partials[4 * blockIdx.x + c] = s;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_mean_final(const double *partials, int nparts, double *out)
+{
+    __shared__ double sh[1024];
+    for (int c = 0; c < 4; ++c) {
+        double v = 0.0;
+        for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += partials[4 * i + c];
+        double s = block_sum<double>(v, sh);
+        if (threadIdx.x == 0) sh[0] = s;
+        if (threadIdx.x == 0) out[c] = s;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        double w = out[3];
+        for (int c = 0; c < 3; ++c) out[c] = w > 0 ? out[c] / w : 0.0;
+    }
+}
+
+// Boundary layout (n1, n2, n3, comp) <-> internal SoA comp-planes with n1 fastest.
+template <typename Tin, typename Tout>
+__global__ void k_aos_to_soa(Geom g, const Tin *__restrict__ a, Tout *__restrict__ s)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= g.n_nodes) return;
+    const int n1 = (int)(n % g.nn1);
+    const long r = n / g.nn1;
+    const int n2 = (int)(r % g.nn2);
+    const int n3 = (int)(r / g.nn2);
+    long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
+    s[n] = (Tout)a[b];
+    s[g.ns + n] = (Tout)a[b + 1];
+    s[2 * g.ns + n] = (Tout)a[b + 2];
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_soa_to_aos(Geom g, const Tin *__restrict__ s, Tout *__restrict__ a)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= g.n_nodes) return;
+    const int n1 = (int)(n % g.nn1);
+    const long r = n / g.nn1;
+    const int n2 = (int)(r % g.nn2);
+    const int n3 = (int)(r / g.nn2);
+    long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
+    a[b] = (Tout)s[n];
+    a[b + 1] = (Tout)s[g.ns + n];
+    a[b + 2] = (Tout)s[2 * g.ns + n];
+}
+
+// Cell fields: boundary (c1, c2, c3[, comp]) -> internal c1-fastest (SoA planes for vectors).
+template <typename Tout>
+__global__ void k_cells_to_internal(Geom g, const double *__restrict__ a, int ncomp, double scale_by_Ms0,
+                                    const double *__restrict__ Ms, Tout *__restrict__ s)
+{
+    long c = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (c >= g.n_cells) return;
+    const int c1 = (int)(c % g.N1);
+    const long r = c / g.N1;
+    const int c2 = (int)(r % g.N2);
+    const int c3 = (int)(r / g.N2);
+    long b = (((long)c1 * g.N2 + c2) * g.N3 + c3) * ncomp;
+    double f = scale_by_Ms0 != 0.0 ? (Ms ? Ms[c] : scale_by_Ms0) : 1.0;
+    for (int j = 0; j < ncomp; ++j) s[j * g.cs + c] = (Tout)(f * a[b + j]);
+}
+
+template <typename Tin, typename Tout>
+__global__ void k_convert(long n, const Tin *__restrict__ a, Tout *__restrict__ b)
+{
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (Tout)a[i];
+}
+
+// volume weights of the nodal mean: sum over adjacent magnetic cells of V/8
+template <typename T>
+__global__ void k_node_volume(Geom g, const double *__restrict__ Ms, double Ms0, double V8, T *vol)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= g.n_nodes) return;
+    const int n1 = (int)(n % g.nn1);
+    const long r = n / g.nn1;
+    const int n2 = (int)(r % g.nn2);
+    const int n3 = (int)(r / g.nn2);
+    double s = 0.0;
+    for (int i = 0; i < 8; ++i) {
+        int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+        if (c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3) {
+            double ms = Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0;
+            if (ms > 0.0) s += V8;
+        }
+    }
+    vol[n] = (T)s;
+}
+
+// ---------------------------------------------------------------------------------------------
+template <typename T>
+void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st)
+{
+    k_stage_input<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, k, ctl, y);
+}
+
+int reduction_blocks(long n_nodes)
+{
+    long b = (n_nodes + kRedThreads - 1) / kRedThreads;
+    return (int)(b > 1024 ? 1024 : (b < 1 ? 1 : b));
+}
+
+template <typename T>
+void launch_dp5_control(const Geom &g, const double *m, const KList &kb, const KList &ke, const T *inv_mass,
+                        StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st)
+{
+    int nb = reduction_blocks(g.n_nodes);
+    k_dp5_err<T><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, kb, ke, inv_mass, ctl, partials);
+    k_dp5_ctl<<<1, 1024, 0, st>>>(partials, nb, n_active, ctl, max_rej);
+}
+
+template <typename T>
+void launch_dp5_update(const Geom &g, double *m, const KList &kb, const T *k7, T *k1, const StepCtl *ctl, int renorm,
+                       cudaStream_t st)
+{
+    k_dp5_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, kb, k7, k1, ctl, renorm);
+}
+
+template <typename T>
+void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, int renorm, cudaStream_t st)
+{
+    k_rk4_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, kb, ctl, renorm);
+    k_rk4_advance<<<1, 1, 0, st>>>(ctl);
+}
+
+template <typename T>
+void launch_mean(const Geom &g, const double *m, const T *vol, double *partials, double *out, cudaStream_t st)
+{
+    int nb = reduction_blocks(g.n_nodes);
+    k_mean_partials<T><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, vol, partials);
+    k_mean_final<<<1, 1024, 0, st>>>(partials, nb, out);
+}
+
+template <typename Tin, typename Tout>
+void launch_aos_to_soa(const Geom &g, const Tin *a, Tout *s, cudaStream_t st)
+{
+    k_aos_to_soa<Tin, Tout><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g, a, s);
+}
+
+template <typename Tin, typename Tout>
+void launch_soa_to_aos(const Geom &g, const Tin *s, Tout *a, cudaStream_t st)
+{
+    k_soa_to_aos<Tin, Tout><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g, s, a);
+}
+
+template <typename Tout>
+void launch_cells_to_internal(const Geom &g, const double *a, int ncomp, double scale_by_Ms0, const double *Ms,
+                              Tout *s, cudaStream_t st)
+{
+    k_cells_to_internal<Tout><<<div_up(g.n_cells, 256), 256, 0, st>>>(g, a, ncomp, scale_by_Ms0, Ms, s);
+}
+
+template <typename Tin, typename Tout>
+void launch_convert(long n, const Tin *a, Tout *b, cudaStream_t st)
+{
+    k_convert<Tin, Tout><<<div_up(n, 256), 256, 0, st>>>(n, a, b);
+}
+
+template <typename T>
+void launch_node_volume(const Geom &g, const double *Ms, double Ms0, double V, T *vol, cudaStream_t st)
+{
+    k_node_volume<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g, Ms, Ms0, V / 8.0, vol);
+}
+
+#define NM_INST(T)                                                                                             \
+    template void launch_stage_input<T>(const Geom &, const double *, const KList &, const StepCtl *, T *,       \
+                                        cudaStream_t);                                                         \
+    template void launch_dp5_control<T>(const Geom &, const double *, const KList &, const KList &, const T *,   \
+                                        StepCtl *, double *, double, int, cudaStream_t);                       \
+    template void launch_dp5_update<T>(const Geom &, double *, const KList &, const T *, T *, const StepCtl *,  \
+                                       int, cudaStream_t);                                                     \
+    template void launch_rk4_update<T>(const Geom &, double *, const KList &, StepCtl *, int, cudaStream_t);    \
+    template void launch_mean<T>(const Geom &, const double *, const T *, double *, double *, cudaStream_t);     \
+    template void launch_cells_to_internal<T>(const Geom &, const double *, int, double, const double *, T *,  \
+                                              cudaStream_t);                                                   \
+    template void launch_node_volume<T>(const Geom &, const double *, double, double, T *, cudaStream_t);
+
+NM_INST(float)
+NM_INST(double)
+template void launch_aos_to_soa<float, float>(const Geom &, const float *, float *, cudaStream_t);
+template void launch_aos_to_soa<double, float>(const Geom &, const double *, float *, cudaStream_t);
+template void launch_aos_to_soa<double, double>(const Geom &, const double *, double *, cudaStream_t);
+template void launch_soa_to_aos<float, float>(const Geom &, const float *, float *, cudaStream_t);
+template void launch_soa_to_aos<float, double>(const Geom &, const float *, double *, cudaStream_t);
+template void launch_soa_to_aos<double, double>(const Geom &, const double *, double *, cudaStream_t);
+template void launch_convert<double, float>(long, const double *, float *, cudaStream_t);
+template void launch_convert<double, double>(long, const double *, double *, cudaStream_t);
+template void launch_convert<float, double>(long, const float *, double *, cudaStream_t);
+
+}  // namespace nm
