@@ -1,0 +1,432 @@
+#!/usr/bin/env python3
+"""Throughput benchmark: LLG node-steps/s of adaptive Dormand-Prince 5(4) integration with the full
+effective field (exchange, uniaxial anisotropy, FFT demag), FP32 field evaluation with FP64 state
+(the library's NM_F32 mode), beside the plain FP64 path, on one GB300 per rank.
+
+One "step" is one DP5 step attempt of the whole hot path: six effective-field evaluations (node->cell
+average, five demag FFT passes, fused local stencil and LLG right-hand side with stage formation),
+the FP64 error norm with device-side step control, and the accepted update with renormalisation.
+
+  python bench.py [--gpus N --steps K --warmup W] [--grid 1024x1024x32] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank integrates its own replica (no data-path
+collective: independent runs shard trivially); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import nm_inputs as inp  # noqa: E402
+
+METRIC = "LLG node-steps/s (h_eff incl. FFT demag) FP32 vs plain FP64; serving p50/p99"
+UNIT = "node-steps/s"
+
+
+# ----------------------------------------------------------------------------------------- helpers
+def parse_grid(s):
+    v = tuple(int(x) for x in s.lower().split("x"))
+    assert len(v) == 3
+    return v
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2411_11725_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(name, stage, n, b, with_maps):
+    """Bytes a launch must move at minimum ('Kernels and their rooflines').
+    n = (N1, N2, N3); b = bytes per real (4 or 8); stage = DP5 stage index of node kernels."""
+    N1, N2, N3 = n
+    Nn = (N1 + 1) * (N2 + 1) * (N3 + 1)
+    Nc = N1 * N2 * N3
+
+    def pad(v):
+        if v == 1:
+            return 1
+        p = 1
+        while p < 2 * v - 1:
+            p *= 2
+        return p
+    P1, P2, P3 = pad(N1), pad(N2), pad(N3)
+    X = P1 // 2 + 1
+    H2, H3 = P2 // 2 + 1, P3 // 2 + 1
+    c = 2 * b  # complex
+    ms = b * Nc if with_maps else 0
+    if name == "demag_x_fwd":
+        return 3 * b * Nn + ms + 3 * c * X * N2 * N3
+    if name == "demag_y_fwd":
+        return 3 * c * X * N2 * N3 + 3 * c * X * P2 * N3
+    if name == "demag_z_conv":
+        return 2 * 3 * c * X * P2 * N3 + 6 * b * X * H2 * H3
+    if name == "demag_y_inv":
+        return 3 * c * X * P2 * N3 + 3 * c * X * N2 * N3
+    if name == "demag_y_conv":
+        return 2 * 3 * c * X * N2 + 6 * b * X * H2
+    if name == "demag_x_inv":
+        return 3 * c * X * N2 * N3 + ms + 3 * b * Nc
+    if name == "node_llg_stage":
+        # y_s, Ms*H_c, 1/mass in; k_s out; for s < 7 also m (FP64), the k_j with non-zero a_{s+1,j}
+        # (j < s), and y_{s+1} out
+        base = 3 * b * Nn + 3 * b * Nc + b * Nn + 3 * b * Nn
+        if stage < 7:
+            nk = {2: 1, 3: 2, 4: 3, 5: 4, 6: 4}[stage]
+            base += 24 * Nn + nk * 3 * b * Nn + 3 * b * Nn
+        return base
+    if name == "stage_input":
+        return 24 * Nn + 3 * b * Nn + 3 * b * Nn
+    if name == "dp5_error_control":
+        return 24 * Nn + 6 * 3 * b * Nn + b * Nn
+    if name == "dp5_update":
+        return 24 * Nn + 6 * 3 * b * Nn + 24 * Nn + 3 * b * Nn
+    return 0
+
+
+def traffic_for(name, workload_key):
+    """dram bytes per launch from the committed ncu summary, if it matches the current kernels."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    if d.get("csrc_sha") != csrc_hash():
+        return None
+    ent = d.get("kernels", {}).get(name)
+    if not ent:
+        return None
+    scale = ent.get("scale_to", {}).get(workload_key)
+    v = ent.get("bytes_per_launch")
+    if v is None:
+        return None
+    return float(v) * (scale if scale else 1.0) if (scale or ent.get("workload") == workload_key) else None
+
+
+# ----------------------------------------------------------------------------------------- arms
+def oracle_sample(seconds=15.0, grid=(32, 32, 4), max_steps=None):
+    """Time the FP64 oracle (direct-sum demag) on a bounded sample: DP5 steps on a smaller cuboid of
+    the same material and cell size.  Returns (node-steps/s, cores, steps, seconds, description)."""
+    import oracle
+    oracle.build()
+    p = inp.throughput(grid, 0)
+    me = oracle.Mesh(p.n, p.dx)
+    me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+    st = me.dp5_stepper(p.m0, 0.0, 1e-15, p.terms, rtol=1e-5, atol=1e-5)
+    me.tensor()  # set-up outside the timed sample
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        st.step()
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > seconds or (max_steps and steps >= max_steps):
+            break
+    nn = int(np.prod(p.nodes))
+    desc = (f"oracle DP5(4) steps on {grid[0]}x{grid[1]}x{grid[2]} cells (same material and 3 nm cells, "
+            f"direct O(N^2) demag, FP64), {steps} steps in {el:.1f} s; the oracle's cost per node grows "
+            f"with N, so this over-states its rate on the full grid")
+    return nn * st.n_acc / el, oracle.num_threads(), steps, el, desc
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    W, K = args.warmup, args.steps
+    import oracle
+    oracle.build()
+    p = inp.throughput((32, 32, 4), 0)
+    me = oracle.Mesh(p.n, p.dx)
+    me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+    me.tensor()
+    st = me.dp5_stepper(p.m0, 0.0, 1e-15, p.terms, rtol=1e-5, atol=1e-5)
+    for _ in range(W):
+        st.step()
+    a0 = st.n_acc
+    t0 = time.perf_counter()
+    for _ in range(K):
+        st.step()
+    el = time.perf_counter() - t0
+    nn = int(np.prod(p.nodes))
+    v = nn * (st.n_acc - a0) / el
+    desc = (f"FP64 CPU oracle, DP5(4) steps on 32x32x4 cells of the throughput material (direct-sum demag); "
+            f"a bounded sample of the {args.grid} workload, which the O(N^2) oracle cannot run")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": el / K * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"cuboid {args.grid} cells, 3 nm, Ms=1e6 A/m, A=1.5e-11 J/m, Ku=5e5 J/m^3 "
+                                   f"along z, DP5(4) rtol=atol=1e-5 (sampled on 32x32x4)"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    import paper_2411_11725_gb300 as nmgb
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    n = parse_grid(args.grid)
+    W, K = args.warmup, args.steps
+    p = inp.throughput(n, seed=rank, with_m0=False)
+    m0 = inp.unit_vectors(np.random.default_rng(rank), p.nodes)
+    nn = int(np.prod(p.nodes))
+    stream = torch.cuda.Stream()
+
+    def make(prec):
+        me = nmgb.Mesh(p.n, p.dx, prec, stream=stream)
+        me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+        me.set_terms(p.terms)
+        me.set_state(m0, 0.0, 1e-15)
+        return me
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed_steps(me, k):
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        a0, r0, _ = me.counters()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        me.run_steps(k, nmgb.DP54, 1e-5, 1e-5)
+        e1.record(stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        a1, r1, err = me.counters()
+        return ms, a1 - a0, r1 - r0
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---- FP32 (mixed) path: the headline
+    me = make(nmgb.F32)
+    me.run_steps(W, nmgb.DP54, 1e-5, 1e-5)
+    me.sync()
+    clk = ClockSampler(local)
+    clk.start()
+    ms, acc, rej = timed_steps(me, K)
+    clocks = clk.stop()
+    ms_max = max_over_ranks(ms)
+    acc_tot = sum_over_ranks(acc)
+    value = nn * acc_tot / (ms_max * 1e-3)
+    # per-launch timing for the roofline (CUDA events between launches on the mesh stream)
+    prof = me.profile_step(nmgb.DP54, reps=3)
+    # ---- e2e: the public API with host buffers, every step: H2D of m, one step, D2H of m
+    m_host = torch.from_numpy(m0.copy()).pin_memory()
+    out_host = torch.empty_like(m_host).pin_memory()
+    me.set_state(m_host.numpy(), 0.0, me.get_state()[2])
+    ke = max(2, min(K, args.e2e_steps))
+    torch.cuda.synchronize()
+    barrier()
+    t_e = time.perf_counter()
+    acc_e = 0
+    dt_e = me.get_state()[2]
+    for _ in range(ke):
+        me.set_state_host_ptr(m_host, 0.0, dt_e)
+        me.run_steps(1, nmgb.DP54, 1e-5, 1e-5)
+        _, dt_e = me.get_state_host_ptr(out_host)
+        acc_e += me.counters()[0]
+    torch.cuda.synchronize()
+    el_e = max_over_ranks(time.perf_counter() - t_e)
+    e2e_value = nn * sum_over_ranks(acc_e) / el_e
+    me.close()
+    del me
+    # ---- plain FP64 path on the same workload (fewer steps: it is several times slower)
+    k64 = max(2, min(K, args.fp64_steps))
+    me = make(nmgb.F64)
+    me.run_steps(min(W, 3), nmgb.DP54, 1e-5, 1e-5)
+    me.sync()
+    ms64, acc64, _ = timed_steps(me, k64)
+    ms64 = max_over_ranks(ms64)
+    value64 = nn * sum_over_ranks(acc64) / (ms64 * 1e-3)
+    me.close()
+    del me
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel (largest share of the step time)
+    b = 4
+    groups = {}
+    stage = 1
+    rows = []
+    for name, t in prof:
+        if name == "node_llg_stage":
+            stage += 1
+        byts = algorithmic_bytes(name, stage, n, b, False)
+        rows.append((name, stage, t, byts))
+        g = groups.setdefault(name, [0.0, 0, 0.0])
+        g[0] += t
+        g[1] += 1
+        g[2] += byts
+    step_ms = sum(r[2] for r in rows)
+    dom = max(groups.items(), key=lambda kv: kv[1][0])
+    dname, (dms, dcount, dbytes) = dom
+    peak, peak_src = measured_peaks()
+    achieved = (dbytes / dcount) / (dms / dcount * 1e-3) / 1e9
+    wl_key = f"{n[0]}x{n[1]}x{n[2]}"
+    traffic = traffic_for(dname, wl_key)
+    step_bytes = sum(r[3] for r in rows)
+    kernels = {k: {"launches_per_step": v[1], "ms_per_launch": v[0] / v[1], "share": v[0] / step_ms,
+                   "GBps": (v[2] / v[1]) / (v[0] / v[1] * 1e-3) / 1e9,
+                   "frac_of_peak": (v[2] / v[1]) / (v[0] / v[1] * 1e-3) / 1e9 / peak}
+               for k, v in groups.items()}
+    launches_per_step = len(prof) + 1  # dp5_error_control is two kernels
+    cpu_v, cores, cs_steps, cs_el, cs_desc = oracle_sample(seconds=args.cpu_seconds)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"cuboid {wl_key} cells of 3 nm, Ms=1e6 A/m, A=1.5e-11 J/m, Ku=5e5 J/m^3 along z, "
+                               f"exchange+anisotropy+FFT demag, random unit m0, DP5(4) rtol=atol=1e-5",
+                   "nodes": nn, "cells": int(np.prod(n)), "precision": "FP32 field evaluation, FP64 state, "
+                   "error norm and step control", "l2": "working set larger than L2 (no flush needed)",
+                   "accepted_steps": int(acc_tot), "rejected_steps": int(sum_over_ranks(rej)),
+                   "parallelism": f"replicas x{world}"},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
+                 "fp32_over_fp64": value / value64},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(24 * nn),
+                "d2h_bytes_per_step": int(24 * nn), "steps": ke,
+                "note": "per step: nm_set_state from pinned host m, one DP5 step (FSAL slope recomputed), "
+                        "nm_get_state to pinned host"},
+        "roofline": {"bound": "hbm", "kernel": dname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "algorithmic_bytes_per_launch": dbytes / dcount,
+                     "step_achieved": step_bytes / (step_ms * 1e-3) / 1e9,
+                     "step_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak},
+        "kernels": kernels,
+        "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cs_desc},
+        "clocks": clocks,
+        "gpu_launches": int(launches_per_step * K),
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--grid", default="1024x1024x32")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    try:
+        run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,13 @@ int nm_run_until(nm_mesh mesh, double t_end, int method, double rtol, double ato
                  double sample_dt, double *samples_out, long max_samples, long *n_accepted,
                  long *n_rejected);
 
+/* Per-launch device times of one integrator step: the step's kernels are launched directly (not from
+ * a graph) on the mesh's stream with CUDA events recorded after each launch, `reps` times on the
+ * resident state (which advances).  Writes the mean milliseconds of launch i to ms_out[i] and its
+ * name to names_out + 32*i (may be NULL), for i < min(*n_kernels, max_kernels).  Synchronises. */
+int nm_profile_step(nm_mesh mesh, int method, int reps, double rtol, double atol, int max_kernels,
+                    double *ms_out, char *names_out, int *n_kernels);
+
 /* Sizes of the mesh: nodes, cells, padded FFT lengths P1 P2 P3, and the device bytes the mesh holds. */
 int nm_mesh_info(nm_mesh mesh, long *n_nodes, long *n_cells, int P[3], long *device_bytes);
 

@@ -64,6 +64,7 @@ SIGNATURES = [
     ("nm_get_counters", _i, [_vp, _Pl, _Pl, _Pd]),
     ("nm_run_until", _i, [_vp, _d, _i, _d, _d, _d, _d, _Pd, _l, _Pl, _Pl]),
     ("nm_mesh_info", _i, [_vp, _Pl, _Pl, _Pi, _Pl]),
+    ("nm_profile_step", _i, [_vp, _i, _i, _d, _d, _i, _Pd, ctypes.c_char_p, _Pi]),
     ("nm_footprint_bytes", _l, [_i, _i, _i, _i]),
     ("nm_sync", _i, [_vp]),
     ("nm_last_error", ctypes.c_char_p, []),
@@ -215,6 +216,22 @@ class Mesh:
                                      ctypes.byref(dt)))
         return out, t.value, dt.value
 
+    def set_state_host_ptr(self, m, t, dt):
+        """Set the state from a contiguous float64 CPU torch tensor (e.g. pinned) without a copy."""
+        if m.dtype != self._torch.float64 or m.is_cuda or not m.is_contiguous() or tuple(m.shape) != self.nodes + (3,):
+            raise ValueError("need a contiguous float64 CPU tensor of the nodal shape")
+        _check(self.lib.nm_set_state(self._h, ctypes.c_void_p(m.data_ptr()), MEM_HOST, float(t), float(dt)))
+
+    def get_state_host_ptr(self, out):
+        """Copy the state into a contiguous float64 CPU torch tensor; returns (t, dt)."""
+        if out.dtype != self._torch.float64 or out.is_cuda or not out.is_contiguous() or \
+                tuple(out.shape) != self.nodes + (3,):
+            raise ValueError("need a contiguous float64 CPU tensor of the nodal shape")
+        t, dt = ctypes.c_double(), ctypes.c_double()
+        _check(self.lib.nm_get_state(self._h, ctypes.c_void_p(out.data_ptr()), MEM_HOST, ctypes.byref(t),
+                                     ctypes.byref(dt)))
+        return t.value, dt.value
+
     def counters(self):
         a, r, e = ctypes.c_long(), ctypes.c_long(), ctypes.c_double()
         _check(self.lib.nm_get_counters(self._h, ctypes.byref(a), ctypes.byref(r), ctypes.byref(e)))
@@ -254,6 +271,20 @@ class Mesh:
 
     def run_steps(self, n_steps, method=DP54, rtol=1e-5, atol=1e-5):
         _check(self.lib.nm_run_steps(self._h, int(method), int(n_steps), float(rtol), float(atol)))
+
+    def profile_step(self, method=DP54, reps=3, rtol=1e-5, atol=1e-5, max_kernels=128):
+        """[(kernel name, mean ms)] of one integrator step, launch by launch (CUDA events)."""
+        ms = np.zeros(max_kernels)
+        names = ctypes.create_string_buffer(32 * max_kernels)
+        nk = ctypes.c_int()
+        _check(self.lib.nm_profile_step(self._h, int(method), int(reps), float(rtol), float(atol), max_kernels,
+                                        _pd(ms), names, ctypes.byref(nk)))
+        raw = names.raw
+        out = []
+        for i in range(min(nk.value, max_kernels)):
+            nm = raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
+            out.append((nm, float(ms[i])))
+        return out
 
     def run_until(self, t_end, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0, sample_dt=0.0):
         """Integrate to t_end; returns (samples (k,3) or None, n_accepted, n_rejected)."""

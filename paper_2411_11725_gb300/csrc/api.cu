@@ -99,7 +99,37 @@ struct nm_mesh_s {
     double n_active = 0;
     long bytes = 0;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+    // per-launch profiling (nm_profile_step)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> prof_ev;
+    std::vector<const char *> prof_names;
+    size_t prof_n = 0;
 };
+
+static void prof_mark_cb(void *ctx, const char *name)
+{
+    nm_mesh M = (nm_mesh)ctx;
+    if (!M->prof_on) return;
+    if (M->prof_n == M->prof_ev.size()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        M->prof_ev.push_back(e);
+        M->prof_names.push_back(name);
+    }
+    M->prof_names[M->prof_n] = name;
+    cudaEventRecord(M->prof_ev[M->prof_n], M->st);
+    ++M->prof_n;
+}
+
+static Marker marker(nm_mesh M)
+{
+    Marker mk;
+    if (M->prof_on) {
+        mk.fn = prof_mark_cb;
+        mk.ctx = M;
+    }
+    return mk;
+}
 
 // --------------------------------------------------------------------------------------------- geometry
 static int pad_len(int n)
@@ -202,6 +232,7 @@ static void release(nm_mesh M)
         if (p) cudaFree(p);
     if (M->hctl) cudaFreeHost(M->hctl);
     if (M->mean_h) cudaFreeHost(M->mean_h);
+    for (cudaEvent_t e : M->prof_ev) cudaEventDestroy(e);
     if (M->own_stream) cudaStreamDestroy(M->st);
     delete M;
 }
@@ -221,12 +252,17 @@ extern "C" int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, do
     if (!out) return fail(NM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n1 < 1 || n2 < 1 || n3 < 1) return fail(NM_ERR_ARG, "cell counts must be >= 1 (got %d %d %d)", n1, n2, n3);
-    if (n1 > 2048 || n2 > 2048 || n3 > 64 || (n3 == 1 && n2 > 1024))
-        return fail(NM_ERR_ARG, "grid %dx%dx%d beyond the supported range (N1, N2 <= 2048; N3 <= 64; N2 <= 1024 "
-                                "for one layer)", n1, n2, n3);
+    if (n1 > 1024 || n2 > 1024 || n3 > 64)
+        return fail(NM_ERR_ARG, "grid %dx%dx%d beyond the supported range (N1, N2 <= 1024; N3 <= 64)", n1, n2, n3);
     if (!(dx1 > 0) || !(dx2 > 0) || !(dx3 > 0) || !isfinite(dx1) || !isfinite(dx2) || !isfinite(dx3))
         return fail(NM_ERR_ARG, "cell sizes must be positive and finite");
     if (precision != NM_F32 && precision != NM_F64) return fail(NM_ERR_ARG, "precision must be NM_F32 or NM_F64");
+    {
+        const Geom gg = make_geom(n1, n2, n3);
+        const bool ok = precision == NM_F64 ? demag_plan<double>(gg).ok : demag_plan<float>(gg).ok;
+        if (!ok)
+            return fail(NM_ERR_ARG, "grid %dx%dx%d exceeds the FFT block budget of this precision", n1, n2, n3);
+    }
     nm_mesh M = new nm_mesh_s();
     M->prec = precision;
     M->rs = precision == NM_F64 ? 8 : 4;
@@ -646,6 +682,7 @@ static DemagBufs<T> demag_bufs(nm_mesh M)
     b.Ms = (const T *)M->Ms_d;
     b.Ms0 = (T)M->Ms0;
     b.ctl = nullptr;
+    b.mark = marker(M);
     return b;
 }
 
@@ -694,6 +731,7 @@ static void enqueue_stage(nm_mesh M, const LocalParams<T> &p, int s, double c_s,
     sa.c_s = c_s;
     sa.ctl = M->ctl;
     launch_llg_stage<T>(p, ys, (T *)M->k[s - 1], ynext, sa, M->st);
+    marker(M)("node_llg_stage");
 }
 
 // k1 = f(m) at the resident time (first DP5 step after a state change)
@@ -716,6 +754,7 @@ static void enqueue_dp5_step(nm_mesh M)
     k2in.a[0] = kDpA[1][0];
     k2in.n = 1;
     launch_stage_input<T>(g, M->m, k2in, M->ctl, (T *)M->y[0], M->st);  // y_2
+    marker(M)("stage_input");
     for (int s = 2; s <= 7; ++s) {
         const T *ys = (const T *)M->y[s % 2];
         T *yn = s < 7 ? (T *)M->y[(s + 1) % 2] : nullptr;
@@ -731,9 +770,11 @@ static void enqueue_dp5_step(nm_mesh M)
     kb.n = ke.n = 6;
     launch_dp5_control<T>(g, M->m, kb, ke, (const T *)M->inv_mass, M->ctl, M->partials, M->n_active, M->max_rej,
                           M->st);
+    marker(M)("dp5_error_control");
     KList ku = kb;
     ku.n = 5;  // b7 = 0
     launch_dp5_update<T>(g, M->m, ku, (const T *)M->k[6], (T *)M->k[0], M->ctl, M->renorm, M->st);
+    marker(M)("dp5_update");
 }
 
 template <typename T>
@@ -743,6 +784,7 @@ static void enqueue_rk4_step(nm_mesh M)
     const Geom &g = M->g;
     KList none{};
     launch_stage_input<T>(g, M->m, none, M->ctl, (T *)M->y[1], M->st);  // y_1 = m
+    marker(M)("stage_input");
     for (int s = 1; s <= 4; ++s) {
         const T *ys = (const T *)M->y[s % 2];
         T *yn = s < 4 ? (T *)M->y[(s + 1) % 2] : nullptr;
@@ -755,6 +797,7 @@ static void enqueue_rk4_step(nm_mesh M)
     }
     kb.n = 4;
     launch_rk4_update<T>(g, M->m, kb, M->ctl, M->renorm, M->st);
+    marker(M)("rk4_update");
 }
 
 static int enqueue_step(nm_mesh M, int method)
@@ -945,5 +988,56 @@ extern "C" int nm_run_until(nm_mesh M, double t_end, int method, double rtol, do
     if ((rc = push_ctl(M))) return rc;
     if (n_accepted) *n_accepted = h->n_acc - acc0;
     if (n_rejected) *n_rejected = h->n_rej - rej0;
+    return NM_OK;
+}
+
+extern "C" int nm_profile_step(nm_mesh M, int method, int reps, double rtol, double atol, int max_kernels,
+                               double *ms_out, char *names_out, int *n_kernels)
+{
+    g_last_error.clear();
+    int rc = check_step_args(M, method, rtol, atol);
+    if (rc) return rc;
+    if (reps < 1 || max_kernels < 1 || !ms_out || !n_kernels) return fail(NM_ERR_ARG, "bad profiling arguments");
+    if ((rc = pull_ctl(M))) return rc;
+    StepCtl *h = M->hctl;
+    h->rtol = rtol;
+    h->atol = atol;
+    h->t_end = 0.0;
+    h->done = 0;
+    h->status = NM_OK;
+    if ((rc = push_ctl(M))) return rc;
+    if ((rc = ensure_k1(M, method))) return rc;
+    free_graphs(M);  // graphs hold no markers
+    std::vector<double> acc;
+    int nk = 0;
+    cudaEvent_t start;
+    CUDA_TRY(cudaEventCreate(&start));
+    for (int r = 0; r < reps; ++r) {
+        M->prof_on = true;
+        M->prof_n = 0;
+        cudaEventRecord(start, M->st);
+        rc = enqueue_step(M, method);
+        M->prof_on = false;
+        if (rc) { cudaEventDestroy(start); return rc; }
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+        nk = (int)M->prof_n;
+        if (acc.empty()) acc.assign(nk, 0.0);
+        cudaEvent_t prev = start;
+        for (int i = 0; i < nk; ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, prev, M->prof_ev[i]);
+            acc[i] += ms;
+            prev = M->prof_ev[i];
+        }
+    }
+    cudaEventDestroy(start);
+    *n_kernels = nk;
+    for (int i = 0; i < nk && i < max_kernels; ++i) {
+        ms_out[i] = acc[i] / reps;
+        if (names_out) {
+            strncpy(names_out + 32 * i, M->prof_names[i], 31);
+            names_out[32 * i + 31] = 0;
+        }
+    }
     return NM_OK;
 }

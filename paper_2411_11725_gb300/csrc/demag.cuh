@@ -30,7 +30,23 @@ struct DemagBufs {
     const T *Ms;               // cell Ms map (SoA, n_cells) or NULL for uniform
     T Ms0;
     const StepCtl *ctl;        // when set, passes do nothing once ctl->done (finished integrations)
+    Marker mark;               // profiling hook
 };
+
+// Launch shapes of the passes (lines per block bounded by the FFT engine's 16 values per thread).
+struct DemagPlan {
+    bool ok;  // the grid fits the engine's per-block budget in this precision
+    int x_lpb, x_threads;
+    size_t x_smem;
+    int y_G, y_threads;
+    size_t y_smem;
+    int z_G, z_KY, z_threads;
+    size_t z_smem;
+    int yc_G, yc_threads;
+    size_t yc_smem;
+};
+template <typename T>
+DemagPlan demag_plan(const Geom &g);
 
 // Demag of the nodal field y (SoA, real T): writes (Ms_c H_c) per cell into MsH (3 x cs).
 template <typename T>

@@ -169,23 +169,25 @@ __global__ void __launch_bounds__(256) k_llg_stage(LocalParams<T> p, const T *__
     k_out[ns + n] = ky;
     k_out[2 * ns + n] = kz;
     if (y_next) {
+        // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working precision,
+        // the addition to the FP64 magnetisation in FP64
         const double dt = sa.ctl ? sa.ctl->dt : 0.0;
-        double ax = 0, ay = 0, az = 0;
+        T ax = 0, ay = 0, az = 0;
         for (int j = 0; j + 1 < sa.s; ++j) {
-            double aj = sa.a[j];
-            if (aj == 0.0) continue;
+            const T aj = (T)sa.a[j];
+            if (aj == T(0)) continue;
             const T *kj = (const T *)sa.k[j];
-            ax += aj * (double)kj[n];
-            ay += aj * (double)kj[ns + n];
-            az += aj * (double)kj[2 * ns + n];
+            ax += aj * kj[n];
+            ay += aj * kj[ns + n];
+            az += aj * kj[2 * ns + n];
         }
-        double as = sa.a[sa.s - 1];
-        ax += as * (double)kx;
-        ay += as * (double)ky;
-        az += as * (double)kz;
-        y_next[n] = (T)(sa.m[n] + dt * ax);
-        y_next[ns + n] = (T)(sa.m[ns + n] + dt * ay);
-        y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * az);
+        const T as = (T)sa.a[sa.s - 1];
+        ax += as * kx;
+        ay += as * ky;
+        az += as * kz;
+        y_next[n] = (T)(sa.m[n] + dt * (double)ax);
+        y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)ay);
+        y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)az);
     }
 }
 

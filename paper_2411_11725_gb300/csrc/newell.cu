@@ -137,7 +137,7 @@ struct LineMap {
     int parity[6];  // +1 even, -1 odd, per component
 };
 
-__global__ void __launch_bounds__(256) k_sym_lines(LineMap lm, const double *__restrict__ in, double *__restrict__ out,
+__global__ void __launch_bounds__(512) k_sym_lines(LineMap lm, const double *__restrict__ in, double *__restrict__ out,
                                                    const Cx<double> *__restrict__ tw, int twlg, int lpb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -146,34 +146,33 @@ __global__ void __launch_bounds__(256) k_sym_lines(LineMap lm, const double *__r
     const long l0 = (long)blockIdx.x * lpb;
     const int nl = (int)min((long)lpb, nlines - l0);
     if (nl <= 0) return;
-    const int P = lm.P, ls = P + 1;
-    for (int t = threadIdx.x; t < nl * P; t += blockDim.x) {
-        int li, j;
-        if (lm.in_es == 1) { li = t / P; j = t % P; }
-        else { li = t % nl; j = t / nl; }
+    const int P = lm.P, lsz = padded_len(P);
+    auto line = [&](int li, int &comp, long &ib, long &ob) {
         long l = l0 + li;
-        int comp = (int)(l / ((long)lm.na * lm.nb));
+        comp = (int)(l / ((long)lm.na * lm.nb));
         long rem = l % ((long)lm.na * lm.nb);
         int ua = (int)(rem / lm.nb), vb = (int)(rem % lm.nb);
-        const double *src = in + comp * lm.in_cs + ua * lm.in_as + vb * lm.in_bs;
+        ib = comp * lm.in_cs + ua * lm.in_as + vb * lm.in_bs;
+        ob = comp * lm.out_cs + ua * lm.out_as + vb * lm.out_bs;
+    };
+    // extended line g[j] = f(j) for j < N, g[P - j] = parity * f(j) for 0 < j < N, else 0
+    auto src = [&](int li, int j) -> Cx<double> {
+        int comp;
+        long ib, ob;
+        line(li, comp, ib, ob);
         double v = 0.0;
-        if (j < lm.N) v = src[j * lm.in_es];
-        else if (P - j < lm.N) v = lm.parity[comp] * src[(P - j) * lm.in_es];
-        buf[li * ls + j] = cx<double>(v, 0.0);
-    }
-    __syncthreads();
-    smem_fft<double, 8>(buf, nl, ls, lm.lgP, -1, tw, twlg);
-    for (int t = threadIdx.x; t < nl * lm.H; t += blockDim.x) {
-        int li, k;
-        if (lm.out_es == 1) { li = t / lm.H; k = t % lm.H; }
-        else { li = t % nl; k = t / nl; }
-        long l = l0 + li;
-        int comp = (int)(l / ((long)lm.na * lm.nb));
-        long rem = l % ((long)lm.na * lm.nb);
-        int ua = (int)(rem / lm.nb), vb = (int)(rem % lm.nb);
-        Cx<double> z = buf[li * ls + k];
-        out[comp * lm.out_cs + ua * lm.out_as + vb * lm.out_bs + k * lm.out_es] = lm.parity[comp] > 0 ? z.x : z.y;
-    }
+        if (j < lm.N) v = in[ib + j * lm.in_es];
+        else if (P - j < lm.N) v = lm.parity[comp] * in[ib + (P - j) * lm.in_es];
+        return cx<double>(v, 0.0);
+    };
+    auto sm = [&](int li, int i) { return li * lsz + pad16(i); };
+    auto dst = [&](int li, int k, Cx<double> z) {
+        int comp;
+        long ib, ob;
+        line(li, comp, ib, ob);
+        out[ob + k * lm.out_es] = lm.parity[comp] > 0 ? z.x : z.y;
+    };
+    fft_lines<double, false, false, false>(buf, nl, lm.lgP, -1, tw, twlg, P, lm.H, src, sm, dst);
 }
 
 template <typename T>
@@ -246,13 +245,15 @@ static int ilog2(int v)
 static cudaError_t sym_pass(const LineMap &lm, const double *in, double *out, const Cx<double> *tw, int twlg,
                             cudaStream_t st)
 {
-    int lpb = 8192 / lm.P;
-    if (lpb < 1) lpb = 1;
+    // lines per block within the FFT engine's budget: lpb * P <= fft_regs<double>() * threads
+    int lpb = fft_regs<double>() * 512 / lm.P;
+    if (lpb < 1) return cudaErrorInvalidConfiguration;
     if (lpb > 64) lpb = 64;
-    size_t sm = (size_t)lpb * (lm.P + 1) * sizeof(Cx<double>);
+    size_t sm = (size_t)lpb * padded_len(lm.P) * sizeof(Cx<double>);
     cudaFuncSetAttribute(k_sym_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     long nlines = 6L * lm.na * lm.nb;
-    k_sym_lines<<<(int)((nlines + lpb - 1) / lpb), 256, sm, st>>>(lm, in, out, tw, twlg, lpb);
+    int nt = (long)lpb * lm.P > (long)fft_regs<double>() * 256 ? 512 : 256;
+    k_sym_lines<<<(int)((nlines + lpb - 1) / lpb), nt, sm, st>>>(lm, in, out, tw, twlg, lpb);
     return cudaGetLastError();
 }
 

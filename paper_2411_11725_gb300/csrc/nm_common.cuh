@@ -3,7 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/nmgb.h"
+#include "nmgb.h"
 
 namespace nm {
 
@@ -47,6 +47,16 @@ struct StepCtl {
     int status;      // NM_OK or an NM_ERR_* code set on the device
     int consecutive_rej;
     double rtol, atol;
+};
+
+// Optional per-launch hook, called after every kernel launch with the kernel's name (profiling).
+struct Marker {
+    void (*fn)(void *ctx, const char *name) = nullptr;
+    void *ctx = nullptr;
+    void operator()(const char *name) const
+    {
+        if (fn) fn(ctx, name);
+    }
 };
 
 // Launch-shape helpers

@@ -7,7 +7,7 @@ namespace nm {
 
 constexpr int kRedThreads = 256;
 
-// y = m + dt * sum_j a_j k_j   (FP64 accumulation; y in the working precision)
+// y = m + dt * sum_j a_j k_j: slope combination in the working precision, addition in FP64
 template <typename T>
 __global__ void k_stage_input(long n_nodes, long ns, const double *__restrict__ m, KList k, const StepCtl *ctl,
                               T *__restrict__ y)
@@ -18,10 +18,18 @@ __global__ void k_stage_input(long n_nodes, long ns, const double *__restrict__ 
     const double dt = ctl->dt;
     for (int c = 0; c < 3; ++c) {
         long i = c * ns + n;
-        double acc = 0.0;
-        for (int j = 0; j < k.n; ++j) acc += k.a[j] * (double)((const T *)k.p[j])[i];
-        y[i] = (T)(m[i] + dt * acc);
+        T acc = 0;
+        for (int j = 0; j < k.n; ++j) acc += (T)k.a[j] * ((const T *)k.p[j])[i];
+        y[i] = (T)(m[i] + dt * (double)acc);
     }
+}
+
+// 1/sqrt(s) for s > 0 in FP64 from an FP32 estimate and one Newton step (relative error ~1e-14), so
+// the FP32 path renormalises without FP64 division or square root.
+__device__ __forceinline__ double rsqrt_refined(double s)
+{
+    const double r0 = (double)rsqrtf((float)s);
+    return r0 * (1.5 - 0.5 * s * r0 * r0);
 }
 
 template <typename T>
@@ -39,7 +47,8 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 }
 
 // Per-block partial sums of ((dt sum_i e_i k_i) / (atol + rtol max(|m|, |m5|)))^2 over magnetic
-// nodes, m5 = m + dt sum_i b_i k_i.
+// nodes, m5 = m + dt sum_i b_i k_i.  The per-node terms follow the working precision of the slopes;
+// the sums are FP64.
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, const double *__restrict__ m,
                                                           KList kb, KList ke, const T *__restrict__ inv_mass,
@@ -51,19 +60,27 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, 
     double acc = 0.0;
     for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < n_nodes; n += (long)gridDim.x * blockDim.x) {
         if (!(inv_mass[n] > T(0))) continue;
+        T part = 0;
         for (int c = 0; c < 3; ++c) {
             long i = c * ns + n;
-            double sb = 0.0, se = 0.0;
+            T sb = 0, se = 0;
             for (int j = 0; j < kb.n; ++j) {
-                double kv = (double)((const T *)kb.p[j])[i];
-                sb += kb.a[j] * kv;
-                se += ke.a[j] * kv;
+                const T kv = ((const T *)kb.p[j])[i];
+                sb += (T)kb.a[j] * kv;
+                se += (T)ke.a[j] * kv;
             }
-            double m0 = m[i], m5 = m0 + dt * sb;
-            double sc = atol + rtol * fmax(fabs(m0), fabs(m5));
-            double q = dt * se / sc;
-            acc += q * q;
+            const double m0 = m[i], m5 = m0 + dt * (double)sb;
+            if (sizeof(T) == 8) {
+                const double sc = atol + rtol * fmax(fabs(m0), fabs(m5));
+                const double q = dt * (double)se / sc;
+                acc += q * q;
+            } else {
+                const T sc = (T)atol + (T)rtol * fmaxf(fabsf((float)m0), fabsf((float)m5));
+                const T q = (T)dt * se / sc;
+                part += q * q;
+            }
         }
+        acc += (double)part;
     }
     double s = block_sum<T>(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -115,6 +132,27 @@ __global__ void __launch_bounds__(1024) k_dp5_ctl(const double *partials, int np
     ctl->dt = dtn;
 }
 
+// m + dt * sum_j b_j k_j, optionally renormalised (FP64 result; slope combination in the working
+// precision, and in the FP32 path the norm through rsqrt_refined)
+template <typename T>
+__device__ __forceinline__ void advance_node(long n, long ns, const double *__restrict__ m, const KList &kb, double dt,
+                                             int renorm, double v[3])
+{
+    for (int c = 0; c < 3; ++c) {
+        long i = c * ns + n;
+        T sb = 0;
+        for (int j = 0; j < kb.n; ++j) sb += (T)kb.a[j] * ((const T *)kb.p[j])[i];
+        v[c] = m[i] + dt * (double)sb;
+    }
+    if (renorm) {
+        const double s = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (s > 0.0) {
+            const double r = sizeof(T) == 8 ? 1.0 / sqrt(s) : rsqrt_refined(s);
+            v[0] *= r; v[1] *= r; v[2] *= r;
+        }
+    }
+}
+
 // Accepted step: m <- m5 (optionally renormalised), k1 <- k7 (FSAL).  Rejected: nothing.
 template <typename T>
 __global__ void k_dp5_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const T *__restrict__ k7,
@@ -123,18 +161,8 @@ __global__ void k_dp5_update(long n_nodes, long ns, double *__restrict__ m, KLis
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
     if (!ctl->accepted) return;
-    const double dt = ctl->dt_used;
     double v[3];
-    for (int c = 0; c < 3; ++c) {
-        long i = c * ns + n;
-        double sb = 0.0;
-        for (int j = 0; j < kb.n; ++j) sb += kb.a[j] * (double)((const T *)kb.p[j])[i];
-        v[c] = m[i] + dt * sb;
-    }
-    if (renorm) {
-        double s = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        if (s > 0.0) { v[0] /= s; v[1] /= s; v[2] /= s; }
-    }
+    advance_node<T>(n, ns, m, kb, ctl->dt_used, renorm, v);
     for (int c = 0; c < 3; ++c) {
         long i = c * ns + n;
         m[i] = v[c];
@@ -149,18 +177,8 @@ __global__ void k_rk4_update(long n_nodes, long ns, double *__restrict__ m, KLis
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
     if (ctl->done) return;
-    const double dt = ctl->dt;
     double v[3];
-    for (int c = 0; c < 3; ++c) {
-        long i = c * ns + n;
-        double sb = 0.0;
-        for (int j = 0; j < kb.n; ++j) sb += kb.a[j] * (double)((const T *)kb.p[j])[i];
-        v[c] = m[i] + dt * sb;
-    }
-    if (renorm) {
-        double s = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
-        if (s > 0.0) { v[0] /= s; v[1] /= s; v[2] /= s; }
-    }
+    advance_node<T>(n, ns, m, kb, ctl->dt, renorm, v);
     for (int c = 0; c < 3; ++c) m[c * ns + n] = v[c];
 }
 
