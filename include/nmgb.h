@@ -153,6 +153,30 @@ int nm_run_until(nm_mesh mesh, double t_end, int method, double rtol, double ato
 int nm_profile_step(nm_mesh mesh, int method, int reps, double rtol, double atol, int max_kernels,
                     double *ms_out, char *names_out, int *n_kernels);
 
+/* Transpose product of the effective field (the gradient of <v, h_eff(m)>), for inverse problems
+ * (section "Inverse Micromagnetics"; static problems differentiate the discretised field, the
+ * discretise-first approach).  m, v: DEVICE real nodal vector fields; grad_m (DEVICE real nodal vector
+ * field) receives J_h(m)^T v; grad_Ms (DEVICE real cell scalar field, or NULL) receives the derivative
+ * of <v, h_eff(m)> with respect to the cell Ms map (through the lumped mass, the Ms-weighted cell->node
+ * averages and the demag source).  The applied field does not depend on m.  Asynchronous.
+ * Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_OOM, NM_ERR_CUDA. */
+int nm_h_eff_vjp(nm_mesh mesh, const void *m, const void *v, unsigned terms, double t, void *grad_m,
+                 void *grad_Ms);
+
+/* Integrate from the resident state to t_end (as nm_run_until) and return a sampled quadratic loss
+ *   L = sum_k sum_{n,j} weight_{n,j} (m_{n,j}(t_k) - target_{n,j})^2
+ * over the sample times t_k = t0 + k sample_dt <= t_end (k >= 1; k = 0 too when include_initial), or
+ * over t_end alone when sample_dt <= 0, together with its exact discrete gradient: the adjoint of every
+ * accepted step with the step sizes of the forward run frozen (backpropagation through the integrator,
+ * section "Automatic Differentiation and Time Integration"), recomputing segments of
+ * `checkpoint_every` steps from stored states (<= 0: 32).  weight, target: HOST FP64 nodal vector
+ * fields (target may be NULL = 0).  Outputs (HOST FP64, each may be NULL except loss): loss; grad_Ms
+ * (cell scalar field, dL/dMs); grad_m0 (nodal vector field, dL/dm(t0)); n_steps (accepted steps).
+ * The resident state ends at t_end.  Synchronises.  Errors: as nm_run_until, NM_ERR_OOM. */
+int nm_adjoint_run(nm_mesh mesh, int method, double t_end, double rtol, double atol, double dt0,
+                   double sample_dt, const double *weight, const double *target, int include_initial,
+                   long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps);
+
 /* Sizes of the mesh: nodes, cells, padded FFT lengths P1 P2 P3, and the device bytes the mesh holds. */
 int nm_mesh_info(nm_mesh mesh, long *n_nodes, long *n_cells, int P[3], long *device_bytes);
 

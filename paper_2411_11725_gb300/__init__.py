@@ -65,6 +65,8 @@ SIGNATURES = [
     ("nm_run_until", _i, [_vp, _d, _i, _d, _d, _d, _d, _Pd, _l, _Pl, _Pl]),
     ("nm_mesh_info", _i, [_vp, _Pl, _Pl, _Pi, _Pl]),
     ("nm_profile_step", _i, [_vp, _i, _i, _d, _d, _i, _Pd, ctypes.c_char_p, _Pi]),
+    ("nm_h_eff_vjp", _i, [_vp, _vp, _vp, _u, _d, _vp, _vp]),
+    ("nm_adjoint_run", _i, [_vp, _i, _d, _d, _d, _d, _d, _Pd, _Pd, _i, _l, _Pd, _Pd, _Pd, _Pl]),
     ("nm_footprint_bytes", _l, [_i, _i, _i, _i]),
     ("nm_sync", _i, [_vp]),
     ("nm_last_error", ctypes.c_char_p, []),
@@ -285,6 +287,36 @@ class Mesh:
             nm = raw[32 * i:32 * i + 32].split(b"\0")[0].decode()
             out.append((nm, float(ms[i])))
         return out
+
+    def h_eff_vjp(self, m, v, terms=ALL, t=0.0, want_Ms=True):
+        """(J_h(m)^T v, d<v, h(m)>/dMs) for nodal CUDA tensors m, v; the second is None unless want_Ms."""
+        torch = self._torch
+        m = m.to(self.dtype).contiguous()
+        v = v.to(self.dtype).contiguous()
+        gm = torch.empty(self.nodes + (3,), dtype=self.dtype, device=self.device)
+        gMs = torch.empty(self.n, dtype=self.dtype, device=self.device) if want_Ms else None
+        self._sync_torch()
+        _check(self.lib.nm_h_eff_vjp(self._h, ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()),
+                                     int(terms), float(t), ctypes.c_void_p(gm.data_ptr()),
+                                     None if gMs is None else ctypes.c_void_p(gMs.data_ptr())))
+        self.sync()
+        return gm, gMs
+
+    def adjoint_run(self, t_end, weight, target=None, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0,
+                    sample_dt=0.0, include_initial=False, checkpoint_every=32):
+        """Forward integration to t_end with the sampled quadratic loss and its discrete adjoint.
+        Returns (loss, dL/dMs (N1,N2,N3), dL/dm0 nodal, accepted steps)."""
+        W = _host_f64(weight, self.nodes + (3,))
+        tg = None if target is None else _host_f64(target, self.nodes + (3,))
+        loss = ctypes.c_double()
+        gMs = np.zeros(self.n)
+        gm0 = np.zeros(self.nodes + (3,))
+        ns = ctypes.c_long()
+        _check(self.lib.nm_adjoint_run(self._h, int(method), float(t_end), float(rtol), float(atol), float(dt0),
+                                       float(sample_dt), _pd(W), _pd(tg), int(bool(include_initial)),
+                                       int(checkpoint_every), ctypes.byref(loss), _pd(gMs), _pd(gm0),
+                                       ctypes.byref(ns)))
+        return loss.value, gMs, gm0, ns.value
 
     def run_until(self, t_end, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0, sample_dt=0.0):
         """Integrate to t_end; returns (samples (k,3) or None, n_accepted, n_rejected)."""

@@ -8,15 +8,11 @@
 #include <string>
 #include <vector>
 
-#include "local.cuh"
-#include "newell.cuh"
-#include "rk.cuh"
-
-using namespace nm;
+#include "mesh.cuh"
 
 static thread_local std::string g_last_error;
 
-static int fail(int code, const char *fmt, ...)
+int fail(int code, const char *fmt, ...)
 {
     char buf[512];
     va_list ap;
@@ -25,110 +21,6 @@ static int fail(int code, const char *fmt, ...)
     va_end(ap);
     g_last_error = buf;
     return code;
-}
-
-#define CUDA_TRY(expr)                                                                                     \
-    do {                                                                                                   \
-        cudaError_t _e = (expr);                                                                           \
-        if (_e != cudaSuccess) return fail(NM_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e),   \
-                                           __FILE__, __LINE__);                                            \
-    } while (0)
-
-#define CHECK_LAUNCH()                                                                                     \
-    do {                                                                                                   \
-        cudaError_t _e = cudaGetLastError();                                                               \
-        if (_e != cudaSuccess) return fail(NM_ERR_CUDA, "kernel launch: %s (%s:%d)", cudaGetErrorString(_e), \
-                                           __FILE__, __LINE__);                                            \
-    } while (0)
-
-// Dormand & Prince (1980) RK5(4)7M coefficients
-static const double kDpC[7] = {0.0, 1.0 / 5, 3.0 / 10, 4.0 / 5, 8.0 / 9, 1.0, 1.0};
-static const double kDpA[7][6] = {
-    {0, 0, 0, 0, 0, 0},
-    {1.0 / 5, 0, 0, 0, 0, 0},
-    {3.0 / 40, 9.0 / 40, 0, 0, 0, 0},
-    {44.0 / 45, -56.0 / 15, 32.0 / 9, 0, 0, 0},
-    {19372.0 / 6561, -25360.0 / 2187, 64448.0 / 6561, -212.0 / 729, 0, 0},
-    {9017.0 / 3168, -355.0 / 33, 46732.0 / 5247, 49.0 / 176, -5103.0 / 18656, 0},
-    {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84}};
-static const double kDpB[7] = {35.0 / 384, 0, 500.0 / 1113, 125.0 / 192, -2187.0 / 6784, 11.0 / 84, 0};
-static const double kDpBs[7] = {5179.0 / 57600, 0, 7571.0 / 16695, 393.0 / 640, -92097.0 / 339200, 187.0 / 2100,
-                                1.0 / 40};
-// classical RK4
-static const double kRk4A[4][3] = {{0, 0, 0}, {0.5, 0, 0}, {0, 0.5, 0}, {0, 0, 1.0}};
-static const double kRk4C[4] = {0.0, 0.5, 0.5, 1.0};
-static const double kRk4B[4] = {1.0 / 6, 1.0 / 3, 1.0 / 3, 1.0 / 6};
-
-struct nm_mesh_s {
-    int prec;
-    size_t rs;  // sizeof(real)
-    cudaStream_t st;
-    bool own_stream;
-    Geom g;
-    double dx[3];
-    // device buffers
-    double *m = nullptr;
-    void *y[2] = {nullptr, nullptr};
-    void *k[7] = {};
-    void *hin = nullptr, *hout = nullptr;
-    void *inv_mass = nullptr, *vol = nullptr;
-    void *MsH = nullptr;
-    void *S = nullptr;
-    void *Nk = nullptr;
-    void *tw = nullptr;
-    Cx<double> *tw64 = nullptr;
-    void *A_d = nullptr, *Ku_d = nullptr, *Ms_d = nullptr;
-    double *Ms64_d = nullptr;
-    void *Msh_d = nullptr;
-    double *hcell64_d = nullptr;
-    StepCtl *ctl = nullptr;
-    StepCtl *hctl = nullptr;  // pinned host mirror
-    double *partials = nullptr;
-    double *mean_d = nullptr;
-    double *mean_h = nullptr;  // pinned
-    unsigned long long *n_active_d = nullptr;
-    // model
-    double A0 = 0, Ku0 = 0, Ms0 = 0, axis[3] = {0, 0, 1}, alpha = 0, gamma = 0;
-    double hu[3] = {0, 0, 0}, hu_freq = 0, hu_phase = 0, hc_freq = 0, hc_phase = 0;
-    bool has_hcell = false;
-    bool material_set = false, state_set = false, k1_valid = false;
-    unsigned terms = NM_ALL;
-    int renorm = 1;
-    double dt_min = 1e-22;
-    int max_rej = 50;
-    double n_active = 0;
-    long bytes = 0;
-    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-    // per-launch profiling (nm_profile_step)
-    bool prof_on = false;
-    std::vector<cudaEvent_t> prof_ev;
-    std::vector<const char *> prof_names;
-    size_t prof_n = 0;
-};
-
-static void prof_mark_cb(void *ctx, const char *name)
-{
-    nm_mesh M = (nm_mesh)ctx;
-    if (!M->prof_on) return;
-    if (M->prof_n == M->prof_ev.size()) {
-        cudaEvent_t e;
-        cudaEventCreate(&e);
-        M->prof_ev.push_back(e);
-        M->prof_names.push_back(name);
-    }
-    M->prof_names[M->prof_n] = name;
-    cudaEventRecord(M->prof_ev[M->prof_n], M->st);
-    ++M->prof_n;
-}
-
-static Marker marker(nm_mesh M)
-{
-    Marker mk;
-    if (M->prof_on) {
-        mk.fn = prof_mark_cb;
-        mk.ctx = M;
-    }
-    return mk;
 }
 
 // --------------------------------------------------------------------------------------------- geometry
@@ -170,6 +62,7 @@ static Geom make_geom(int n1, int n2, int n3)
     g.twlg = ilog2i(mx);
     g.s_comp = (long)n3 * g.P2 * g.Xp;
     g.t_comp = (long)g.H3 * g.H2 * g.Xp;
+    g.n2f = FastDiv((unsigned)n2);
     return g;
 }
 
@@ -201,7 +94,7 @@ static void fill_twiddles(int twlg, std::vector<Cx<T>> &tw)
     }
 }
 
-static int dev_alloc(nm_mesh M, void **p, size_t bytes)
+int dev_alloc(nm_mesh M, void **p, size_t bytes)
 {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
     if (e != cudaSuccess) {
@@ -212,7 +105,7 @@ static int dev_alloc(nm_mesh M, void **p, size_t bytes)
     return NM_OK;
 }
 
-static void free_graphs(nm_mesh M)
+void free_graphs(nm_mesh M)
 {
     for (auto &gx : M->graph)
         if (gx) { cudaGraphExecDestroy(gx); gx = nullptr; }
@@ -225,10 +118,13 @@ static void release(nm_mesh M)
     free_graphs(M);
     void *ptrs[] = {M->m, M->y[0], M->y[1], M->hin, M->hout, M->inv_mass, M->vol, M->MsH, M->S, M->Nk, M->tw,
                     M->tw64, M->A_d, M->Ku_d, M->Ms_d, M->Ms64_d, M->Msh_d, M->hcell64_d, M->ctl, M->partials,
-                    M->mean_d, M->n_active_d};
+                    M->mean_d, M->n_active_d, M->vj_w, M->vj_h, M->vj_q, M->vj_g, M->vj_H, M->vj_HW, M->vj_M,
+                    M->vj_gMs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (void *p : M->k)
+        if (p) cudaFree(p);
+    for (void *p : M->extra)
         if (p) cudaFree(p);
     if (M->hctl) cudaFreeHost(M->hctl);
     if (M->mean_h) cudaFreeHost(M->mean_h);
@@ -581,13 +477,13 @@ extern "C" int nm_set_state(nm_mesh M, const double *m, int where, double t, dou
     return NM_OK;
 }
 
-static int pull_ctl(nm_mesh M)
+int pull_ctl(nm_mesh M)
 {
     CUDA_TRY(cudaMemcpyAsync(M->hctl, M->ctl, sizeof(StepCtl), cudaMemcpyDeviceToHost, M->st));
     CUDA_TRY(cudaStreamSynchronize(M->st));
     return NM_OK;
 }
-static int push_ctl(nm_mesh M)
+int push_ctl(nm_mesh M)
 {
     CUDA_TRY(cudaMemcpyAsync(M->ctl, M->hctl, sizeof(StepCtl), cudaMemcpyHostToDevice, M->st));
     return NM_OK;
@@ -633,60 +529,6 @@ extern "C" int nm_get_counters(nm_mesh M, long *n_accepted, long *n_rejected, do
 
 // --------------------------------------------------------------------------------------------- field pipeline
 template <typename T>
-static LocalParams<T> local_params(nm_mesh M, unsigned terms)
-{
-    LocalParams<T> p{};
-    p.g = M->g;
-    const double *dx = M->dx;
-    const double V = dx[0] * dx[1] * dx[2];
-    for (int d = 0; d < 8; ++d) {
-        const int dd[3] = {(d >> 2) & 1, (d >> 1) & 1, d & 1};
-        double kk = 0.0, mm = V;
-        for (int k = 0; k < 3; ++k) mm *= dd[k] ? 1.0 / 6.0 : 1.0 / 3.0;
-        for (int k = 0; k < 3; ++k) {
-            double v = (dd[k] ? -1.0 : 1.0) / dx[k];
-            for (int l = 0; l < 3; ++l)
-                if (l != k) v *= dx[l] * (dd[l] ? 1.0 / 6.0 : 1.0 / 3.0);
-            kk += v;
-        }
-        p.Wex[d] = (T)(2.0 * kk);
-        p.Wm[d] = (T)mm;
-    }
-    p.mu0V8 = (T)(kMu0 * V / 8.0);
-    p.A = (const T *)M->A_d;
-    p.Ku = (const T *)M->Ku_d;
-    p.Ms = (const T *)M->Ms_d;
-    p.A0 = (T)M->A0;
-    p.Ku0 = (T)M->Ku0;
-    p.Ms0 = (T)M->Ms0;
-    p.e0 = (T)M->axis[0]; p.e1 = (T)M->axis[1]; p.e2 = (T)M->axis[2];
-    p.inv_mass = (const T *)M->inv_mass;
-    p.MsH = (terms & NM_DEMAG) ? (const T *)M->MsH : nullptr;
-    p.Msh = M->has_hcell ? (const T *)M->Msh_d : nullptr;
-    p.hu0 = M->hu[0]; p.hu1 = M->hu[1]; p.hu2 = M->hu[2];
-    p.hu_freq = M->hu_freq; p.hu_phase = M->hu_phase;
-    p.hc_freq = M->hc_freq; p.hc_phase = M->hc_phase;
-    p.terms = terms;
-    p.gam = M->gamma / (1.0 + M->alpha * M->alpha);
-    p.alpha = M->alpha;
-    return p;
-}
-
-template <typename T>
-static DemagBufs<T> demag_bufs(nm_mesh M)
-{
-    DemagBufs<T> b;
-    b.S = (Cx<T> *)M->S;
-    b.Nk = (const T *)M->Nk;
-    b.tw = (const Cx<T> *)M->tw;
-    b.Ms = (const T *)M->Ms_d;
-    b.Ms0 = (T)M->Ms0;
-    b.ctl = nullptr;
-    b.mark = marker(M);
-    return b;
-}
-
-template <typename T>
 static int heff_t(nm_mesh M, const void *m, void *h_out, unsigned terms, double t)
 {
     const Geom &g = M->g;
@@ -726,7 +568,10 @@ static void enqueue_stage(nm_mesh M, const LocalParams<T> &p, int s, double c_s,
     StageArgs sa{};
     sa.m = M->m;
     for (int j = 0; j < 7; ++j) sa.k[j] = M->k[j];
-    for (int j = 0; j < n_next; ++j) sa.a[j] = a_next[j];
+    for (int j = 0; j < n_next; ++j) {
+        sa.a[j] = a_next[j];
+        sa.af[j] = (float)a_next[j];
+    }
     sa.s = s;
     sa.c_s = c_s;
     sa.ctl = M->ctl;
@@ -813,7 +658,7 @@ static int enqueue_step(nm_mesh M, int method)
     return NM_OK;
 }
 
-static int launch_step(nm_mesh M, int method)
+int launch_step(nm_mesh M, int method)
 {
     cudaGraphExec_t &gx = M->graph[method];
     if (!gx) {
@@ -834,7 +679,7 @@ static int launch_step(nm_mesh M, int method)
     return NM_OK;
 }
 
-static int ensure_k1(nm_mesh M, int method)
+int ensure_k1(nm_mesh M, int method)
 {
     if (method != NM_DP54 || M->k1_valid) return NM_OK;
     if (M->prec == NM_F64) enqueue_k1<double>(M);
@@ -844,7 +689,7 @@ static int ensure_k1(nm_mesh M, int method)
     return NM_OK;
 }
 
-static int check_step_args(nm_mesh M, int method, double rtol, double atol)
+int check_step_args(nm_mesh M, int method, double rtol, double atol)
 {
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     if (method != NM_RK4 && method != NM_DP54) return fail(NM_ERR_ARG, "unknown method %d", method);

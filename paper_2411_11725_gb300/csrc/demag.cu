@@ -4,26 +4,27 @@
 // fuses forward y, the product and inverse y), and a pruned complex-to-real x transform that writes
 // Ms_c H_c per cell.
 //
-// Every pass reads its input in the first FFT stage straight from global memory (the zero padding is
-// never read) and writes its output from the last stage straight to global memory (outputs that no
-// later pass needs are never written); shared memory only carries the exchanges between stages.
+// The x passes read their input in the first FFT stage straight from global memory (the zero padding
+// is never read); the y and z passes stage their strided tiles in shared memory with cp.async (all
+// copies of a tile in flight at once).  Every pass writes its output from the last FFT stage straight
+// to global memory, and only the part that later passes read.
 #include "demag.cuh"
 #include "fft.cuh"
 
 namespace nm {
 
+constexpr int kFftThreads = 256;
+
 // ---------------------------------------------------------------------------------------------
 // node -> cell average times Ms for the cell pair (x, x+1) of one cell row:
 // M_c = Ms_c * (1/8) sum_{i in {0,1}^3} y_{c+i}
 template <typename T>
-__device__ __forceinline__ Cx<T> cell_M_pair(const Geom &g, const DemagBufs<T> &b, const T *__restrict__ yc, int x,
-                                             int yy, int zz)
+__device__ __forceinline__ Cx<T> cell_M_pair(const Geom &g, const DemagBufs<T> &b, const T *__restrict__ yc,
+                                             long r00, long c0, int x)
 {
-    const long r00 = ((long)zz * g.nn2 + yy) * g.nn1 + x;
     const long r01 = r00 + g.nn1;
     const long r10 = r00 + (long)g.nn2 * g.nn1;
     const long r11 = r10 + g.nn1;
-    const long c0 = ((long)zz * g.N2 + yy) * g.N1 + x;
     const T a0 = (yc[r00] + yc[r01]) + (yc[r10] + yc[r11]);
     const T a1 = (yc[r00 + 1] + yc[r01 + 1]) + (yc[r10 + 1] + yc[r11 + 1]);
     const T Ms0 = b.Ms ? b.Ms[c0] : b.Ms0;
@@ -36,11 +37,24 @@ __device__ __forceinline__ Cx<T> cell_M_pair(const Geom &g, const DemagBufs<T> &
     return cx<T>(m0, m1);
 }
 
+// Line L of the x passes is (cell row, component) = (L / 3, L % 3); cell row = zz * N2 + yy.
+struct XLine {
+    int c, yy, zz, row;
+};
+__device__ __forceinline__ XLine x_line(const Geom &g, int L)
+{
+    XLine x;
+    x.row = L / 3;
+    x.c = L - 3 * x.row;
+    x.zz = (int)g.n2f.div((unsigned)x.row);
+    x.yy = x.row - x.zz * g.N2;
+    return x;
+}
+
 // Pass 1: x transform (R2C of length P1 via a complex FFT of length Q = P1/2 on even/odd pairs).
-// Lines are (cell row (y, z), component) pairs, line index = 3 * row + component; one block holds
-// `lpb` consecutive lines.  CELL_IN: the input is already a cell field.
+// One block holds `lpb` consecutive lines.  CELL_IN: the input is already a cell field.
 template <typename T, bool CELL_IN>
-__global__ void __launch_bounds__(512) k_x_fwd(Geom g, DemagBufs<T> b, const T *__restrict__ in, int lpb)
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_x_fwd(Geom g, DemagBufs<T> b, const T *__restrict__ in, int lpb)
 {
     if (b.ctl && b.ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -49,47 +63,46 @@ __global__ void __launch_bounds__(512) k_x_fwd(Geom g, DemagBufs<T> b, const T *
     const int l0 = blockIdx.x * lpb;
     const int nl = min(lpb, nlines - l0);
     if (nl <= 0) return;
-    auto pair = [&](int c, int x, int yy, int zz) -> Cx<T> {
+    auto pair = [&](const XLine &xl, int x) -> Cx<T> {
+        const long c0 = (long)xl.row * g.N1 + x;
         if (CELL_IN) {
-            const T *p = in + c * g.cs + ((long)zz * g.N2 + yy) * g.N1 + x;
+            const T *p = in + xl.c * g.cs + c0;
             return cx<T>(p[0], x + 1 < g.N1 ? p[1] : T(0));
         }
-        return cell_M_pair(g, b, in + c * g.ns, x, yy, zz);
+        const long r00 = ((long)xl.zz * g.nn2 + xl.yy) * g.nn1 + x;
+        return cell_M_pair(g, b, in + xl.c * g.ns, r00, c0, x);
     };
     if (g.P1 == 1) {
         for (int t = threadIdx.x; t < nl; t += blockDim.x) {
-            const int L = l0 + t, row = L / 3, c = L - 3 * row;
-            const int yy = row % g.N2, zz = row / g.N2;
-            b.S[c * g.s_comp + ((long)zz * g.P2 + yy) * g.Xp] = cx<T>(pair(c, 0, yy, zz).x, T(0));
+            const XLine xl = x_line(g, l0 + t);
+            b.S[xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp] = cx<T>(pair(xl, 0).x, T(0));
         }
         return;
     }
     const int Q = g.Q, lsz = padded_len(Q);
-    auto src = [&](int l, int i) -> Cx<T> {
-        const int L = l0 + l, row = L / 3, c = L - 3 * row;
-        return pair(c, 2 * i, row % g.N2, row / g.N2);
-    };
+    auto src = [&](int l, int i) -> Cx<T> { return pair(x_line(g, l0 + l), 2 * i); };
     auto sm = [&](int l, int i) { return l * lsz + pad16(i); };
     auto dst = [&](int l, int i, Cx<T> v) { buf[l * lsz + pad16(i)] = v; };
-    fft_lines<T, false, false, true>(buf, nl, g.lgQ, -1, b.tw, g.twlg, (g.N1 + 1) >> 1, Q, src, sm, dst);
+    fft_lines<T, false, false, true>(buf, FastDiv((unsigned)nl), g.lgQ, -1, b.tw, g.twlg, (g.N1 + 1) >> 1, Q, src,
+                                     sm, dst);
     // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}),  W = e^{-2 pi i / P1},  k = 0..Q
     const int wsh = g.twlg - (g.lgQ + 1);
+    const FastDiv qf((unsigned)(Q + 1));
     for (int t = threadIdx.x; t < nl * (Q + 1); t += blockDim.x) {
-        const int k = t % (Q + 1), l = t / (Q + 1);
-        const int L = l0 + l, row = L / 3, c = L - 3 * row;
-        const int yy = row % g.N2, zz = row / g.N2;
+        const int l = (int)qf.div((unsigned)t), k = t - l * (Q + 1);
+        const XLine xl = x_line(g, l0 + l);
         const Cx<T> Zk = buf[l * lsz + pad16(k == Q ? 0 : k)];
         const Cx<T> Zc = conj(buf[l * lsz + pad16(k == 0 ? 0 : Q - k)]);
         const Cx<T> E = scale(Zk + Zc, T(0.5));
         const Cx<T> O = scale(mul_si(Zk - Zc, -1), T(0.5));
-        b.S[c * g.s_comp + ((long)zz * g.P2 + yy) * g.Xp + k] = E + b.tw[k << wsh] * O;
+        b.S[xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp + k] = E + b.tw[k << wsh] * O;
     }
 }
 
 // Pass 5: inverse x transform (C2R of length P1 via a complex FFT of length Q), keeping x < N1.
 // Lines as in pass 1.  Output per cell: Ms_c H_c (or H_c when CELL_OUT).
 template <typename T, bool CELL_OUT>
-__global__ void __launch_bounds__(512) k_x_inv(Geom g, DemagBufs<T> b, T *__restrict__ out, int lpb)
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_x_inv(Geom g, DemagBufs<T> b, T *__restrict__ out, int lpb)
 {
     if (b.ctl && b.ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -104,9 +117,8 @@ __global__ void __launch_bounds__(512) k_x_inv(Geom g, DemagBufs<T> b, T *__rest
     };
     if (g.P1 == 1) {
         for (int t = threadIdx.x; t < nl; t += blockDim.x) {
-            const int L = l0 + t, row = L / 3, c = L - 3 * row;
-            const int yy = row % g.N2, zz = row / g.N2;
-            put(c, ((long)zz * g.N2 + yy) * g.N1, b.S[c * g.s_comp + ((long)zz * g.P2 + yy) * g.Xp].x);
+            const XLine xl = x_line(g, l0 + t);
+            put(xl.c, (long)xl.row * g.N1, b.S[xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp].x);
         }
         return;
     }
@@ -114,26 +126,27 @@ __global__ void __launch_bounds__(512) k_x_inv(Geom g, DemagBufs<T> b, T *__rest
     const int wsh = g.twlg - (g.lgQ + 1);
     // Z_k = (X_k + conj X_{Q-k}) + i e^{2 pi i k / P1} (X_k - conj X_{Q-k}), k < Q
     auto src = [&](int l, int k) -> Cx<T> {
-        const int L = l0 + l, row = L / 3, c = L - 3 * row;
-        const Cx<T> *s = b.S + c * g.s_comp + ((long)(row / g.N2) * g.P2 + row % g.N2) * g.Xp;
+        const XLine xl = x_line(g, l0 + l);
+        const Cx<T> *s = b.S + xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp;
         const Cx<T> Xk = s[k], Xc = conj(s[Q - k]);
         return (Xk + Xc) + mul_si((Xk - Xc) * conj(b.tw[k << wsh]), 1);
     };
     auto sm = [&](int l, int i) { return l * lsz + pad16(i); };
     auto dst = [&](int l, int j, Cx<T> v) {
-        const int L = l0 + l, row = L / 3, c = L - 3 * row;
-        const long cell = (long)row * g.N1 + 2 * j;  // row = zz * N2 + yy
-        put(c, cell, v.x);
-        if (2 * j + 1 < g.N1) put(c, cell + 1, v.y);
+        const XLine xl = x_line(g, l0 + l);
+        const long cell = (long)xl.row * g.N1 + 2 * j;
+        put(xl.c, cell, v.x);
+        if (2 * j + 1 < g.N1) put(xl.c, cell + 1, v.y);
     };
-    fft_lines<T, false, false, false>(buf, nl, g.lgQ, +1, b.tw, g.twlg, Q, (g.N1 + 1) >> 1, src, sm, dst);
+    fft_lines<T, false, false, false>(buf, FastDiv((unsigned)nl), g.lgQ, +1, b.tw, g.twlg, Q, (g.N1 + 1) >> 1, src,
+                                      sm, dst);
 }
 
 // Passes 2 and 4: y transform of G consecutive kx columns of one (component, z) plane, in place.
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
 // The rows are staged with cp.async (all in flight at once), the last stage writes global memory.
 template <typename T>
-__global__ void __launch_bounds__(512) k_y(Geom g, DemagBufs<T> b, int G, int dir)
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_y(Geom g, DemagBufs<T> b, int G, int dir)
 {
     if (b.ctl && b.ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -143,9 +156,9 @@ __global__ void __launch_bounds__(512) k_y(Geom g, DemagBufs<T> b, int G, int di
     const int Xp = g.Xp;
     const int rowb = G * (int)sizeof(Cx<T>);
     const int cb = rowb >= 16 ? 16 : rowb;  // bytes per async copy
-    const int cpr = rowb / cb;
-    for (int t = threadIdx.x; t < nin * cpr; t += blockDim.x) {
-        const int y = t / cpr, ch = t - y * cpr;
+    const int lcpr = __ffs(rowb / cb) - 1;  // copies per row is a power of two
+    for (int t = threadIdx.x; t < (nin << lcpr); t += blockDim.x) {
+        const int y = t >> lcpr, ch = t - (y << lcpr);
         char *d = (char *)(buf + pad16(y) * G) + ch * cb;
         const char *s = (const char *)(base + y * Xp) + ch * cb;
         if (cb == 16) cp_async16(d, s);
@@ -156,125 +169,155 @@ __global__ void __launch_bounds__(512) k_y(Geom g, DemagBufs<T> b, int G, int di
     auto sm = [&](int l, int i) { return pad16(i) * G + l; };
     auto sm_src = [&](int l, int i) { return buf[pad16(i) * G + l]; };
     auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    fft_lines<T, true, true, false>(buf, G, g.lgP2, dir, b.tw, g.twlg, nin, nout, sm_src, sm, dst);
+    fft_lines<T, true, true, false>(buf, FastDiv((unsigned)G), g.lgP2, dir, b.tw, g.twlg, nin, nout, sm_src, sm, dst);
 }
 
-// H^ = N~ M^ at one frequency; N~ real symmetric, stored on the octant with the odd components'
-// signs restored here (Nxy odd in ky, Nxz odd in kz, Nyz odd in both).
+// The six real tensor components at octant frequency (kx, a2, kz), with the sign of the odd ones in
+// kz restored (Nxz odd in kz, Nyz odd in kz); the y parity is applied by the caller (s2).
 template <typename T>
-__device__ __forceinline__ void tensor_apply(const Geom &g, const DemagBufs<T> &b, int kx, int ky, int kz, Cx<T> &mx,
-                                             Cx<T> &my, Cx<T> &mz)
+struct Ten6 {
+    T xx, yy, zz, xy, xz, yz;
+};
+template <typename T>
+__device__ __forceinline__ Ten6<T> tensor_at(const Geom &g, const DemagBufs<T> &b, int kx, int a2, int kz)
 {
-    const int h2 = g.P2 >> 1, h3 = g.P3 >> 1;
-    const int a2 = ky <= h2 ? ky : g.P2 - ky;
+    const int h3 = g.P3 >> 1;
     const int a3 = kz <= h3 ? kz : g.P3 - kz;
-    const T s2 = ky <= h2 ? T(1) : T(-1);
     const T s3 = kz <= h3 ? T(1) : T(-1);
     const T *n = b.Nk + ((long)a3 * g.H2 + a2) * g.Xp + kx;
     const long tc = g.t_comp;
-    const T nxx = n[0], nyy = n[tc], nzz = n[2 * tc];
-    const T nxy = n[3 * tc] * s2, nxz = n[4 * tc] * s3, nyz = n[5 * tc] * (s2 * s3);
-    const Cx<T> hx = cx<T>(nxx * mx.x + nxy * my.x + nxz * mz.x, nxx * mx.y + nxy * my.y + nxz * mz.y);
-    const Cx<T> hy = cx<T>(nxy * mx.x + nyy * my.x + nyz * mz.x, nxy * mx.y + nyy * my.y + nyz * mz.y);
-    const Cx<T> hz = cx<T>(nxz * mx.x + nyz * my.x + nzz * mz.x, nxz * mx.y + nyz * my.y + nzz * mz.y);
-    mx = hx; my = hy; mz = hz;
+    Ten6<T> t;
+    t.xx = n[0]; t.yy = n[tc]; t.zz = n[2 * tc];
+    t.xy = n[3 * tc]; t.xz = n[4 * tc] * s3; t.yz = n[5 * tc] * s3;
+    return t;
+}
+// H^ = N~ M^ with N~ real symmetric; s2 = -1 on the mirrored frequency P2 - a2 (Nxy and Nyz odd in ky)
+template <typename T>
+__device__ __forceinline__ void tensor_mul(const Ten6<T> &t, T s2, Cx<T> *px, Cx<T> *py, Cx<T> *pz)
+{
+    const Cx<T> mx = *px, my = *py, mz = *pz;
+    const T nxy = t.xy * s2, nyz = t.yz * s2;
+    *px = cx<T>(t.xx * mx.x + nxy * my.x + t.xz * mz.x, t.xx * mx.y + nxy * my.y + t.xz * mz.y);
+    *py = cx<T>(nxy * mx.x + t.yy * my.x + nyz * mz.x, nxy * mx.y + t.yy * my.y + nyz * mz.y);
+    *pz = cx<T>(t.xz * mx.x + nyz * my.x + t.zz * mz.x, t.xz * mx.y + nyz * my.y + t.zz * mz.y);
 }
 
-// Pass 3 (N3 > 1): for G kx columns and KY ky rows: forward z (N3 non-zero inputs), tensor product,
-// inverse z keeping z < N3.  Lines l = (c * KY + kyl) * G + g, innermost in shared memory.
+// Pass 3 (N3 > 1): G kx columns x KY octant rows a2 (each with its mirror P2 - a2, so the tensor is
+// read once): forward z (N3 non-zero inputs), tensor product, inverse z keeping z < N3.
+// Rows r < KY are ky = a2_0 + r, rows KY + r are ky = P2 - (a2_0 + r) (present when 0 < a2 < P2/2).
+// Lines l = (c * 2KY + r) * G + g, innermost in shared memory.
 template <typename T>
-__global__ void __launch_bounds__(512) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
 {
     if (b.ctl && b.ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
-    const int kx0 = blockIdx.x * G, ky0 = blockIdx.y * KY;
-    const int nl = 3 * KY * G;
-    auto gaddr = [&](int l, int z) -> long {
-        const int gg = l % G, r = l / G, kyl = r % KY, c = r / KY;
-        return c * g.s_comp + ((long)z * g.P2 + ky0 + kyl) * g.Xp + kx0 + gg;
+    const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
+    const int R2 = 2 * KY, nl = 3 * R2 * G;
+    const int h2 = g.P2 >> 1;
+    auto row_ky = [&](int r) -> int {  // -1: row absent
+        const int a2 = a20 + (r < KY ? r : r - KY);
+        if (a2 >= g.H2) return -1;
+        if (r < KY) return a2;
+        return (a2 > 0 && a2 < h2) ? g.P2 - a2 : -1;
     };
-    auto sm = [&](int l, int i) { return pad16(i) * nl + l; };
-    auto sm_src = [&](int l, int i) { return buf[pad16(i) * nl + l]; };
-    auto dst = [&](int l, int z, Cx<T> v) { b.S[gaddr(l, z)] = v; };
+    auto gaddr = [&](int c, int ky, int z) -> long {
+        return c * g.s_comp + ((long)z * g.P2 + ky) * g.Xp + kx0;
+    };
     {
-        // rows (z, c, kyl) of G complex values, staged with cp.async
         const int rowb = G * (int)sizeof(Cx<T>);
-        const int cb = rowb >= 16 ? 16 : rowb, cpr = rowb / cb;
-        const int nrow = g.N3 * 3 * KY;
-        for (int t = threadIdx.x; t < nrow * cpr; t += blockDim.x) {
-            const int rr = t / cpr, ch = t - rr * cpr;
-            const int kyl = rr % KY, c = (rr / KY) % 3, z = rr / (3 * KY);
-            const int l = (c * KY + kyl) * G;
-            char *d = (char *)(buf + pad16(z) * nl + l) + ch * cb;
-            const char *s = (const char *)(b.S + gaddr(l, z)) + ch * cb;
+        const int cb = rowb >= 16 ? 16 : rowb, lcpr = __ffs(rowb / cb) - 1, lR2 = __ffs(R2) - 1;
+        const int nrow = g.N3 * 3 * R2;
+        for (int t = threadIdx.x; t < (nrow << lcpr); t += blockDim.x) {
+            const int rr = t >> lcpr, ch = t - (rr << lcpr);
+            const int r = rr & (R2 - 1), cz = rr >> lR2, z = cz / 3, c = cz - 3 * z;
+            const int ky = row_ky(r);
+            if (ky < 0) continue;
+            char *d = (char *)(buf + pad16(z) * nl + (c * R2 + r) * G) + ch * cb;
+            const char *s = (const char *)(b.S + gaddr(c, ky, z)) + ch * cb;
             if (cb == 16) cp_async16(d, s);
             else cp_async8(d, s);
         }
         cp_async_wait_all();
         __syncthreads();
     }
-    fft_lines<T, true, true, true>(buf, nl, g.lgP3, -1, b.tw, g.twlg, g.N3, g.P3, sm_src, sm, [&](int l, int i, Cx<T> v) { buf[pad16(i) * nl + l] = v; });
+    const FastDiv nlf((unsigned)nl);
+    auto sm = [&](int l, int i) { return pad16(i) * nl + l; };
+    auto sm_src = [&](int l, int i) { return buf[pad16(i) * nl + l]; };
+    auto sm_dst = [&](int l, int i, Cx<T> v) { buf[pad16(i) * nl + l] = v; };
+    fft_lines<T, true, true, true>(buf, nlf, g.lgP3, -1, b.tw, g.twlg, g.N3, g.P3, sm_src, sm, sm_dst);
     const int npts = KY * G * g.P3;
+    const int lG = __ffs(G) - 1, lKY = __ffs(KY) - 1;
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
-        const int gg = t % G, r = t / G, kyl = r % KY, kz = r / KY;
-        const int l0 = kyl * G + gg;
-        Cx<T> *px = buf + pad16(kz) * nl + l0;
-        Cx<T> *py = px + KY * G;
-        Cx<T> *pz = py + KY * G;
-        Cx<T> mx = *px, my = *py, mz = *pz;
-        tensor_apply(g, b, kx0 + gg, ky0 + kyl, kz, mx, my, mz);
-        *px = mx; *py = my; *pz = mz;
+        const int gg = t & (G - 1), q = t >> lG, rr = q & (KY - 1), kz = q >> lKY;
+        const int a2 = a20 + rr;
+        if (a2 >= g.H2) continue;
+        const Ten6<T> ten = tensor_at(g, b, kx0 + gg, a2, kz);
+        Cx<T> *p = buf + pad16(kz) * nl + rr * G + gg;
+        tensor_mul(ten, T(1), p, p + R2 * G, p + 2 * R2 * G);
+        if (a2 > 0 && a2 < h2) {
+            Cx<T> *pm = p + KY * G;
+            tensor_mul(ten, T(-1), pm, pm + R2 * G, pm + 2 * R2 * G);
+        }
     }
     __syncthreads();
-    fft_lines<T, true, true, false>(buf, nl, g.lgP3, +1, b.tw, g.twlg, g.P3, g.N3, sm_src, sm, dst);
+    auto dst = [&](int l, int z, Cx<T> v) {
+        const int gg = l & (G - 1), q = l >> lG, r = q & (R2 - 1), c = q >> (lKY + 1);
+        const int ky = row_ky(r);
+        if (ky >= 0) b.S[gaddr(c, ky, z) + gg] = v;
+    };
+    fft_lines<T, true, true, false>(buf, nlf, g.lgP3, +1, b.tw, g.twlg, g.P3, g.N3, sm_src, sm, dst);
 }
 
-// Single-layer variant (N3 == 1, P3 == 1): forward y, tensor product at kz = 0, inverse y.
-// Lines l = c * G + g.
+// Single-layer variant (N3 == 1, P3 == 1): forward y, tensor product at kz = 0 (each octant row a2
+// read once and applied to ky = a2 and P2 - a2), inverse y.  Lines l = c * G + g.
 template <typename T>
-__global__ void __launch_bounds__(512) k_y_conv(Geom g, DemagBufs<T> b, int G)
+__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_y_conv(Geom g, DemagBufs<T> b, int G)
 {
     if (b.ctl && b.ctl->done) return;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G;
     const int nl = 3 * G;
-    auto gaddr = [&](int l, int y) -> long {
-        const int gg = l % G, c = l / G;
-        return c * g.s_comp + (long)y * g.Xp + kx0 + gg;
-    };
-    auto sm = [&](int l, int i) { return pad16(i) * nl + l; };
-    auto sm_dst = [&](int l, int i, Cx<T> v) { buf[pad16(i) * nl + l] = v; };
-    auto sm_src = [&](int l, int i) { return buf[pad16(i) * nl + l]; };
-    auto dst = [&](int l, int y, Cx<T> v) { b.S[gaddr(l, y)] = v; };
+    const int h2 = g.P2 >> 1;
+    auto gaddr = [&](int c, int y) -> long { return c * g.s_comp + (long)y * g.Xp + kx0; };
     {
         const int rowb = G * (int)sizeof(Cx<T>);
-        const int cb = rowb >= 16 ? 16 : rowb, cpr = rowb / cb;
+        const int cb = rowb >= 16 ? 16 : rowb, lcpr = __ffs(rowb / cb) - 1;
         const int nrow = g.N2 * 3;
-        for (int t = threadIdx.x; t < nrow * cpr; t += blockDim.x) {
-            const int rr = t / cpr, ch = t - rr * cpr;
-            const int c = rr % 3, y = rr / 3;
+        for (int t = threadIdx.x; t < (nrow << lcpr); t += blockDim.x) {
+            const int rr = t >> lcpr, ch = t - (rr << lcpr);
+            const int y = rr / 3, c = rr - 3 * y;
             char *d = (char *)(buf + pad16(y) * nl + c * G) + ch * cb;
-            const char *s = (const char *)(b.S + gaddr(c * G, y)) + ch * cb;
+            const char *s = (const char *)(b.S + gaddr(c, y)) + ch * cb;
             if (cb == 16) cp_async16(d, s);
             else cp_async8(d, s);
         }
         cp_async_wait_all();
         __syncthreads();
     }
-    fft_lines<T, true, true, true>(buf, nl, g.lgP2, -1, b.tw, g.twlg, g.N2, g.P2, sm_src, sm, sm_dst);
-    for (int t = threadIdx.x; t < G * g.P2; t += blockDim.x) {
-        const int gg = t % G, ky = t / G;
-        Cx<T> *px = buf + pad16(ky) * nl + gg;
-        Cx<T> *py = px + G;
-        Cx<T> *pz = py + G;
-        Cx<T> mx = *px, my = *py, mz = *pz;
-        tensor_apply(g, b, kx0 + gg, ky, 0, mx, my, mz);
-        *px = mx; *py = my; *pz = mz;
+    const FastDiv nlf((unsigned)nl);
+    auto sm = [&](int l, int i) { return pad16(i) * nl + l; };
+    auto sm_src = [&](int l, int i) { return buf[pad16(i) * nl + l]; };
+    auto sm_dst = [&](int l, int i, Cx<T> v) { buf[pad16(i) * nl + l] = v; };
+    fft_lines<T, true, true, true>(buf, nlf, g.lgP2, -1, b.tw, g.twlg, g.N2, g.P2, sm_src, sm, sm_dst);
+    const int lG = __ffs(G) - 1;
+    for (int t = threadIdx.x; t < G * g.H2; t += blockDim.x) {
+        const int gg = t & (G - 1), a2 = t >> lG;
+        const Ten6<T> ten = tensor_at(g, b, kx0 + gg, a2, 0);
+        Cx<T> *p = buf + pad16(a2) * nl + gg;
+        tensor_mul(ten, T(1), p, p + G, p + 2 * G);
+        if (a2 > 0 && a2 < h2) {
+            Cx<T> *pm = buf + pad16(g.P2 - a2) * nl + gg;
+            tensor_mul(ten, T(-1), pm, pm + G, pm + 2 * G);
+        }
     }
     __syncthreads();
-    fft_lines<T, true, true, false>(buf, nl, g.lgP2, +1, b.tw, g.twlg, g.P2, g.N2, sm_src, sm, dst);
+    auto dst = [&](int l, int y, Cx<T> v) {
+        const int gg = l & (G - 1), c = l >> lG;
+        b.S[gaddr(c, y) + gg] = v;
+    };
+    fft_lines<T, true, true, false>(buf, nlf, g.lgP2, +1, b.tw, g.twlg, g.P2, g.N2, sm_src, sm, dst);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -294,65 +337,60 @@ void demag_init_attributes()
     done = true;
 }
 
-static int pow2_floor(int v)
+static int pow2_floor(long v)
 {
     int p = 1;
-    while (p * 2 <= v) p *= 2;
+    while (2L * p <= v) p *= 2;
     return p;
 }
 
-// threads for a block transforming `elems` complex values (fft_regs<T>() per thread), 256 or 512
-template <typename T>
-static int threads_for(long elems)
-{
-    return elems > (long)fft_regs<T>() * 256 ? 512 : 256;
-}
-
+// Launch shapes: every block transforms at most fft_regs<T>() * kFftThreads complex values.
 template <typename T>
 DemagPlan demag_plan(const Geom &g)
 {
     DemagPlan p{};
     p.ok = true;
     const size_t cs = sizeof(Cx<T>);
-    const long kMaxElems = (long)fft_regs<T>() * 512;
+    const long budget = (long)fft_regs<T>() * kFftThreads;
     const int nlines = 3 * g.N2 * g.N3;
     {
         const int Q = g.P1 == 1 ? 1 : g.Q;
-        int lpb = (int)(kMaxElems / Q);
+        int lpb = (int)(budget / Q);
         if (lpb < 1) p.ok = false;
         lpb = lpb < 1 ? 1 : lpb;
         lpb = lpb > 48 ? 48 : lpb;
         lpb = lpb > nlines ? nlines : lpb;
         p.x_lpb = lpb;
-        p.x_threads = threads_for<T>((long)lpb * Q);
+        p.x_threads = kFftThreads;
         p.x_smem = g.P1 == 1 ? 0 : (size_t)lpb * padded_len(Q) * cs;
     }
     if (g.N3 > 1) {
-        int G = pow2_floor((int)(kMaxElems / g.P2));
-        if ((long)G * g.P2 > kMaxElems) p.ok = false;
+        int G = pow2_floor(budget / g.P2);
+        if ((long)G * g.P2 > budget) p.ok = false;
         G = G > 16 ? 16 : G;
         p.y_G = G;
-        p.y_threads = threads_for<T>((long)G * g.P2);
+        p.y_threads = kFftThreads;
         p.y_smem = (size_t)padded_len(g.P2) * G * cs;
-        int Gz = pow2_floor((int)(kMaxElems / (3L * g.P3)));
+        int Gz = pow2_floor(budget / (6L * g.P3));
+        if (6L * Gz * g.P3 > budget) p.ok = false;
         Gz = Gz > 16 ? 16 : Gz;
-        if (3L * Gz * g.P3 > kMaxElems) p.ok = false;
-        int KY = pow2_floor((int)(kMaxElems / (3L * Gz * g.P3)));
-        KY = KY > g.P2 ? g.P2 : KY;
+        int KY = pow2_floor(budget / (6L * Gz * g.P3));
+        KY = KY > g.H2 ? pow2_floor(g.H2) : KY;
         p.z_G = Gz;
         p.z_KY = KY;
-        p.z_threads = threads_for<T>(3L * KY * Gz * g.P3);
-        p.z_smem = (size_t)padded_len(g.P3) * 3 * KY * Gz * cs;
+        p.z_threads = kFftThreads;
+        p.z_smem = (size_t)padded_len(g.P3) * 6 * KY * Gz * cs;
     } else {
-        int G = pow2_floor((int)(kMaxElems / (3L * g.P2)));
-        if (3L * G * g.P2 > kMaxElems) p.ok = false;
+        int G = pow2_floor(budget / (3L * g.P2));
+        if (3L * G * g.P2 > budget) p.ok = false;
         G = G > 16 ? 16 : G;
         p.yc_G = G;
-        p.yc_threads = threads_for<T>(3L * G * g.P2);
+        p.yc_threads = kFftThreads;
         p.yc_smem = (size_t)padded_len(g.P2) * 3 * G * cs;
     }
-    // every grid dimension divides Xp (a multiple of 16)
-    if (g.Xp % (g.N3 > 1 ? (p.y_G > p.z_G ? p.y_G : p.z_G) : p.yc_G) != 0) p.ok = false;
+    // the kx grouping divides Xp (a multiple of 16)
+    const int Gmax = g.N3 > 1 ? (p.y_G > p.z_G ? p.y_G : p.z_G) : p.yc_G;
+    if (g.Xp % Gmax != 0) p.ok = false;
     if (p.x_smem > 200 * 1024 || p.y_smem > 200 * 1024 || p.z_smem > 200 * 1024 || p.yc_smem > 200 * 1024)
         p.ok = false;
     return p;
@@ -371,7 +409,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
             k_y<T><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G, -1);
             b.mark("demag_y_fwd");
         }
-        k_z_conv<T><<<dim3(g.Xp / p.z_G, div_up(g.P2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b, p.z_G, p.z_KY);
+        k_z_conv<T><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b, p.z_G, p.z_KY);
         b.mark("demag_z_conv");
         if (g.P2 > 1) {
             k_y<T><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G, +1);

@@ -20,6 +20,7 @@ struct Geom {
     int twlg;                  // log2 of the twiddle table length
     long s_comp;               // component stride of the spectrum buffer = N3 * P2 * Xp
     long t_comp;               // component stride of the tensor spectrum = H3 * H2 * Xp
+    FastDiv n2f;               // division by N2 (cell row -> (y, z))
 };
 
 template <typename T>

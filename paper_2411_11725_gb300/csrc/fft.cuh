@@ -1,8 +1,7 @@
-// Block-level power-of-two FFT engine (Stockham autosort, radices 8/4/2 in FP32, 4/2 in FP64).
+// Block-level power-of-two FFT engine (Stockham autosort, radices 8, 4 and 2).
 //
 // Each thread keeps fft_regs<T>() complex values of the transform in registers per stage (one
-// butterfly of the largest radix, or several smaller ones), so a length-2048 FP32 transform takes four
-// stages.  The first stage reads its inputs through a caller functor (normally straight from global
+// butterfly of the largest radix, or several smaller ones), so a length-2048 transform takes four stages.  The first stage reads its inputs through a caller functor (normally straight from global
 // memory, skipping the zero padding) and the last stage writes through another functor (normally
 // straight to global memory, skipping outputs nobody reads); only the exchanges between stages go
 // through shared memory.  Shared-memory layouts insert one pad slot after every 16 elements so that
@@ -64,19 +63,21 @@ struct RegDft {
                     const int q = k * (8 / h);  // W_{2h}^k = W_16^q
                     if (q == 0) x[s + k + h] = d;
                     else if (q == 4) x[s + k + h] = mul_si(d, dir);
-                    else x[s + k + h] = d * cx<T>((T)c16(q), (T)(dir * s16(q)));
+                    else {
+                        const T cq = (T)c16(q), sq = (T)s16(q);
+                        x[s + k + h] = d * cx<T>(cq, dir > 0 ? sq : -sq);
+                    }
                 }
             }
         }
     }
 };
 
-// complex values per thread per stage (largest radix): 8 in FP32, 4 in FP64 (keeps the FFT kernels
-// free of register spills at 512 threads per block)
+// complex values per thread per stage (largest radix 8)
 template <typename T>
 __host__ __device__ constexpr int fft_regs()
 {
-    return sizeof(T) == 4 ? 8 : 4;
+    return 8;
 }
 
 // Asynchronous global -> shared copies (cp.async): many in flight per thread without registers.
@@ -115,9 +116,10 @@ __host__ __device__ constexpr int padded_len(int L) { return L + (L >> 4) + 1; }
 //   SYNC_OUT: barrier after the writes (the next stage reads them)
 //   LF:       map consecutive threads to consecutive lines (layouts with lines innermost)
 template <typename T, int R, bool LF, bool SYNC_IN, bool SYNC_OUT, typename Src, typename Dst>
-__device__ __forceinline__ void fft_stage(int nl, int lg, int slg, int dir, const Cx<T> *__restrict__ tw, int twlg,
-                                          int nin, int nout, Src src, Dst dst)
+__device__ __forceinline__ void fft_stage(const FastDiv &nlf, int lg, int slg, int dir, const Cx<T> *__restrict__ tw,
+                                          int twlg, int nin, int nout, Src src, Dst dst)
 {
+    const int nl = (int)nlf.d;
     constexpr int lgR = R == 16 ? 4 : (R == 8 ? 3 : (R == 4 ? 2 : 1));
     constexpr int BPT = fft_regs<T>() / R;
     const int L = 1 << lg, LR = L >> lgR;
@@ -129,8 +131,8 @@ __device__ __forceinline__ void fft_stage(int nl, int lg, int slg, int dir, cons
     for (int c = 0; c < BPT; ++c) {
         const int b = threadIdx.x + c * nt;
         if (b < nb) {
-            const int l = LF ? b % nl : b >> (lg - lgR);
-            const int j = LF ? b / nl : b & (LR - 1);
+            const int j = LF ? (int)nlf.div(b) : b & (LR - 1);
+            const int l = LF ? b - j * nl : b >> (lg - lgR);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int i = j + r * LR;
@@ -143,8 +145,8 @@ __device__ __forceinline__ void fft_stage(int nl, int lg, int slg, int dir, cons
     for (int c = 0; c < BPT; ++c) {
         const int b = threadIdx.x + c * nt;
         if (b < nb) {
-            const int l = LF ? b % nl : b >> (lg - lgR);
-            const int j = LF ? b / nl : b & (LR - 1);
+            const int j = LF ? (int)nlf.div(b) : b & (LR - 1);
+            const int l = LF ? b - j * nl : b >> (lg - lgR);
             const int k = j & (Ns - 1);
             if (k) {
                 const int sh = twlg - slg - lgR;
@@ -173,8 +175,9 @@ __host__ __device__ __forceinline__ int stage_lg(int lg, int s, int rmax)
 __host__ __device__ __forceinline__ int n_stages(int lg, int rmax) { return lg == 0 ? 0 : (lg + rmax - 1) / rmax; }
 
 template <typename T, bool LF, bool SYNC_IN, bool SYNC_OUT, typename Src, typename Dst>
-__device__ __forceinline__ void fft_stage_any(int rl, int nl, int lg, int slg, int dir, const Cx<T> *__restrict__ tw,
-                                              int twlg, int nin, int nout, Src src, Dst dst)
+__device__ __forceinline__ void fft_stage_any(int rl, const FastDiv &nl, int lg, int slg, int dir,
+                                              const Cx<T> *__restrict__ tw, int twlg, int nin, int nout, Src src,
+                                              Dst dst)
 {
     switch (rl) {
     case 4:
@@ -195,9 +198,10 @@ __device__ __forceinline__ void fft_stage_any(int rl, int nl, int lg, int slg, i
 // SRC_SM / DST_SM: src / dst are the same shared buffer (barriers are then placed around them); the
 // caller synchronises before a shared-memory source.  Needs nl * 2^lg <= fft_regs<T>() * blockDim.x.
 template <typename T, bool LF, bool SRC_SM, bool DST_SM, typename Src, typename SmAddr, typename Dst>
-__device__ __forceinline__ void fft_lines(Cx<T> *buf, int nl, int lg, int dir, const Cx<T> *__restrict__ tw,
+__device__ __forceinline__ void fft_lines(Cx<T> *buf, const FastDiv &nlf, int lg, int dir, const Cx<T> *__restrict__ tw,
                                           int twlg, int nin, int nout, Src src, SmAddr sm, Dst dst)
 {
+    const int nl = (int)nlf.d;
     auto sm_src = [&](int l, int i) { return buf[sm(l, i)]; };
     auto sm_dst = [&](int l, int i, Cx<T> v) { buf[sm(l, i)] = v; };
     constexpr int rmax = fft_regs<T>() == 16 ? 4 : (fft_regs<T>() == 8 ? 3 : 2);
@@ -220,7 +224,7 @@ __device__ __forceinline__ void fft_lines(Cx<T> *buf, int nl, int lg, int dir, c
         return;
     }
     if (ns == 1) {
-        fft_stage_any<T, LF, SRC_SM && DST_SM, DST_SM>(stage_lg(lg, 0, rmax), nl, lg, 0, dir, tw, twlg, nin, nout, src,
+        fft_stage_any<T, LF, SRC_SM && DST_SM, DST_SM>(stage_lg(lg, 0, rmax), nlf, lg, 0, dir, tw, twlg, nin, nout, src,
                                                         dst);
         return;
     }
@@ -228,11 +232,11 @@ __device__ __forceinline__ void fft_lines(Cx<T> *buf, int nl, int lg, int dir, c
     for (int s = 0; s < ns; ++s) {
         const int rl = stage_lg(lg, s, rmax);
         if (s == 0)
-            fft_stage_any<T, LF, SRC_SM, true>(rl, nl, lg, slg, dir, tw, twlg, nin, 1 << lg, src, sm_dst);
+            fft_stage_any<T, LF, SRC_SM, true>(rl, nlf, lg, slg, dir, tw, twlg, nin, 1 << lg, src, sm_dst);
         else if (s + 1 < ns)
-            fft_stage_any<T, LF, true, true>(rl, nl, lg, slg, dir, tw, twlg, 1 << lg, 1 << lg, sm_src, sm_dst);
+            fft_stage_any<T, LF, true, true>(rl, nlf, lg, slg, dir, tw, twlg, 1 << lg, 1 << lg, sm_src, sm_dst);
         else
-            fft_stage_any<T, LF, DST_SM, DST_SM>(rl, nl, lg, slg, dir, tw, twlg, 1 << lg, nout, sm_src, dst);
+            fft_stage_any<T, LF, DST_SM, DST_SM>(rl, nlf, lg, slg, dir, tw, twlg, 1 << lg, nout, sm_src, dst);
         slg += rl;
     }
 }

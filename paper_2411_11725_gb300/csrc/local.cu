@@ -26,8 +26,25 @@ struct NodeField {
     bool magnetic;
 };
 
+// Applied-field factors at time t, computed once per block: (h_uniform * s_u(t), s_c(t)).
 template <typename T>
-__device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const T *__restrict__ y, long n, double t)
+__device__ __forceinline__ void block_field_factors(const LocalParams<T> &p, double t, T out[4])
+{
+    __shared__ T sh[4];
+    if (threadIdx.x == 0) {
+        const double su = time_factor<T>(p.hu_freq, p.hu_phase, t);
+        sh[0] = (T)(p.hu0 * su);
+        sh[1] = (T)(p.hu1 * su);
+        sh[2] = (T)(p.hu2 * su);
+        sh[3] = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
+    }
+    __syncthreads();
+    out[0] = sh[0]; out[1] = sh[1]; out[2] = sh[2]; out[3] = sh[3];
+}
+
+template <typename T>
+__device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const T *__restrict__ y, long n,
+                                                   const T hf[4])
 {
     const Geom &g = p.g;
     const int n1 = (int)(n % g.nn1);
@@ -103,7 +120,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
             }
     }
     if (p.Msh && (p.terms & NM_ZEE)) {
-        T sc = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
+        const T sc = hf[3];
         T ax = 0, ay = 0, az = 0;
 #pragma unroll
         for (int i = 0; i < 8; ++i)
@@ -116,14 +133,20 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
         cy_ += sc * ay;
         cz_ += sc * az;
     }
+    if (p.raw) {
+        // -dE itself (the transpose products of the adjoint): no lumped-mass division
+        f.hx = hx + p.mu0V8 * cx_;
+        f.hy = hy + p.mu0V8 * cy_;
+        f.hz = hz + p.mu0V8 * cz_;
+        return f;
+    }
     hx = im * (hx + p.mu0V8 * cx_);
     hy = im * (hy + p.mu0V8 * cy_);
     hz = im * (hz + p.mu0V8 * cz_);
     if (f.magnetic && (p.terms & NM_ZEE)) {
-        double su = time_factor<T>(p.hu_freq, p.hu_phase, t);
-        hx += (T)(p.hu0 * su);
-        hy += (T)(p.hu1 * su);
-        hz += (T)(p.hu2 * su);
+        hx += hf[0];
+        hy += hf[1];
+        hz += hf[2];
     }
     f.hx = hx; f.hy = hy; f.hz = hz;
     return f;
@@ -132,9 +155,11 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 template <typename T>
 __global__ void __launch_bounds__(256) k_heff(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ h, double t)
 {
+    T hf[4];
+    block_field_factors(p, t, hf);
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= p.g.n_nodes) return;
-    NodeField<T> f = node_field(p, y, n, t);
+    NodeField<T> f = node_field(p, y, n, hf);
     const long ns = p.g.ns;
     h[n] = f.hx;
     h[ns + n] = f.hy;
@@ -145,11 +170,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_llg_stage(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ k_out,
                                                    T *__restrict__ y_next, StageArgs sa)
 {
+    if (sa.ctl && sa.ctl->done) return;
+    const double t = sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed;
+    T hf[4];
+    block_field_factors(p, t, hf);
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= p.g.n_nodes) return;
-    double t = sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed;
-    if (sa.ctl && sa.ctl->done) return;
-    NodeField<T> f = node_field(p, y, n, t);
+    NodeField<T> f = node_field(p, y, n, hf);
     const long ns = p.g.ns;
     T kx = 0, ky = 0, kz = 0;
     if (f.magnetic) {
@@ -174,14 +201,14 @@ __global__ void __launch_bounds__(256) k_llg_stage(LocalParams<T> p, const T *__
         const double dt = sa.ctl ? sa.ctl->dt : 0.0;
         T ax = 0, ay = 0, az = 0;
         for (int j = 0; j + 1 < sa.s; ++j) {
-            const T aj = (T)sa.a[j];
+            const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
             if (aj == T(0)) continue;
             const T *kj = (const T *)sa.k[j];
             ax += aj * kj[n];
             ay += aj * kj[ns + n];
             az += aj * kj[2 * ns + n];
         }
-        const T as = (T)sa.a[sa.s - 1];
+        const T as = sizeof(T) == 4 ? (T)sa.af[sa.s - 1] : (T)sa.a[sa.s - 1];
         ax += as * kx;
         ay += as * ky;
         az += as * kz;

@@ -24,6 +24,7 @@ struct LocalParams {
     double hu0, hu1, hu2, hu_freq, hu_phase, hc_freq, hc_phase;
     unsigned terms;
     double gam;        // gamma / (1 + alpha^2)
+    int raw;           // 1: output -dE (no division by the mass, no uniform applied field)
     double alpha;
 };
 
@@ -37,7 +38,7 @@ struct StageArgs {
     double a[8];              // a_{s+1, j}, j = 1 .. s
     int s;                    // stage index (1-based) of the slope being computed
     double c_s;               // time fraction of stage s
-    double c_next;            // unused by kernels; kept for bookkeeping
+    float af[8];              // the same coefficients in FP32 (used by the FP32 path)
     const StepCtl *ctl;       // t, dt
     double t_fixed;           // time when ctl == NULL
 };

@@ -137,7 +137,7 @@ struct LineMap {
     int parity[6];  // +1 even, -1 odd, per component
 };
 
-__global__ void __launch_bounds__(512) k_sym_lines(LineMap lm, const double *__restrict__ in, double *__restrict__ out,
+__global__ void __launch_bounds__(512, 1) k_sym_lines(LineMap lm, const double *__restrict__ in, double *__restrict__ out,
                                                    const Cx<double> *__restrict__ tw, int twlg, int lpb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(512) k_sym_lines(LineMap lm, const double *__r
         line(li, comp, ib, ob);
         out[ob + k * lm.out_es] = lm.parity[comp] > 0 ? z.x : z.y;
     };
-    fft_lines<double, false, false, false>(buf, nl, lm.lgP, -1, tw, twlg, P, lm.H, src, sm, dst);
+    fft_lines<double, false, false, false>(buf, FastDiv((unsigned)nl), lm.lgP, -1, tw, twlg, P, lm.H, src, sm, dst);
 }
 
 template <typename T>
@@ -252,7 +252,7 @@ static cudaError_t sym_pass(const LineMap &lm, const double *in, double *out, co
     size_t sm = (size_t)lpb * padded_len(lm.P) * sizeof(Cx<double>);
     cudaFuncSetAttribute(k_sym_lines, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     long nlines = 6L * lm.na * lm.nb;
-    int nt = (long)lpb * lm.P > (long)fft_regs<double>() * 256 ? 512 : 256;
+    const int nt = 512;
     k_sym_lines<<<(int)((nlines + lpb - 1) / lpb), nt, sm, st>>>(lm, in, out, tw, twlg, lpb);
     return cudaGetLastError();
 }

@@ -28,6 +28,19 @@ template <typename T> __host__ __device__ __forceinline__ Cx<T> mul_si(Cx<T> a, 
     return s > 0 ? cx<T>(-a.y, a.x) : cx<T>(a.y, -a.x);
 }
 
+// Division by a run-time constant through a multiply-high (round-up method): valid for n + d < 2^32.
+struct FastDiv {
+    unsigned d, m, s;
+    FastDiv() = default;
+    __host__ __device__ explicit FastDiv(unsigned d_) : d(d_), m(0), s(0)
+    {
+        while ((1u << s) < d) ++s;
+        m = (unsigned)(((1ull << 32) * ((1ull << s) - d)) / d + 1);
+    }
+    __device__ __forceinline__ unsigned div(unsigned n) const { return (__umulhi(n, m) + n) >> s; }
+    __device__ __forceinline__ unsigned mod(unsigned n) const { return n - div(n) * d; }
+};
+
 // Device-resident step control: every kernel of an RK step reads t and dt from here, so a whole step
 // (or many) can be launched without a host round trip.
 struct StepCtl {
