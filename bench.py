@@ -9,6 +9,10 @@ the FP64 error norm with device-side step control, and the accepted update with 
 
   python bench.py [--gpus N --steps K --warmup W] [--grid 1024x1024x32] [--impl ours|reference]
 
+The line also carries `serving`: Poisson streams of mixed-size LLG runs (grids 64..256 x 64..256 x 1..8
+cells, per-run material, field and duration) through the library's request loop at 0.7x and 1.2x the
+one-at-a-time capacity, with p50/p99 latency, throughput and occupancy (--serve-requests 0 skips it).
+
 Prints one JSON line (rank 0).  Under torchrun every rank integrates its own replica (no data-path
 collective: independent runs shard trivially); the time is the max over ranks.
 """
@@ -368,6 +372,9 @@ def run_ours(args, rank, world, dist):
                    "frac_of_peak": (v[2] / v[1]) / (v[0] / v[1] * 1e-3) / 1e9 / peak}
                for k, v in groups.items()}
     launches_per_step = len(prof) + 1  # dp5_error_control is two kernels
+    serving = None
+    if args.serve_requests > 0:
+        serving = run_serving(args.serve_requests, int(args.serve_budget_gb * (1 << 30)), args.serve_max_active)
     cpu_v, cores, cs_steps, cs_el, cs_desc = oracle_sample(seconds=args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -392,10 +399,71 @@ def run_ours(args, rank, world, dist):
                      "step_frac": step_bytes / (step_ms * 1e-3) / 1e9 / peak},
         "kernels": kernels,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cs_desc},
+        "serving": serving,
         "clocks": clocks,
         "gpu_launches": int(launches_per_step * K),
     }
     print(json.dumps(line), flush=True)
+
+
+def serving_kwargs(i, p):
+    return dict(n=p.n, dx=p.dx, m0=inp.serving_m0(p), t_end=p.extra["t_end"], Ms=p.Ms, A=p.A, Ku=p.Ku,
+                axis=p.axis, alpha=p.alpha, gamma=p.gamma, h=p.h_uniform, terms=p.terms, rtol=p.extra["rtol"],
+                atol=p.extra["atol"], dt0=p.extra["dt0"], tag=i)
+
+
+def run_serving(n_requests, budget_bytes, max_active, loads=(0.7, 1.2), n_capacity=8):
+    """Poisson streams of mixed-size LLG runs through the library's request loop.  Capacity = 1 / mean
+    service time of runs executed one at a time; each load level replays the same requests with arrival
+    rate = load x capacity.  Latency = submit -> result on the host."""
+    from paper_2411_11725_gb300.serve import Server, replay
+    reqs = inp.serving_requests(max(n_requests, n_capacity), seed=0, rate_hz=1.0)
+    stream = [(t, serving_kwargs(i, p)) for i, (t, p) in enumerate(reqs[:n_requests])]
+    nodes = {i: int(np.prod(p.nodes)) for i, (_, p) in enumerate(reqs)}
+    out = {"requests": n_requests, "hbm_budget_bytes": int(budget_bytes), "max_active": max_active,
+           "distribution": "grids N1,N2 in {64,128,256} x N3 in {1,2,4,8} cells of 3 nm, Ms~U[4e5,1.2e6], "
+                           "A~U[5e-12,2e-11], alpha~U[0.01,0.5], |mu0 h|~U[0,100] mT, T~U[0.2,2] ns, "
+                           "DP5(4) rtol=atol=1e-5, FP32 field, seed 0"}
+    with Server(budget_bytes, max_active=max_active) as s:
+        # warm the mesh pool: one short run per shape (tensor spectra resident, as in steady state)
+        shapes = {}
+        for i, (_, kw) in enumerate(stream):
+            shapes.setdefault(tuple(kw["n"]), i)
+        for i in shapes.values():
+            s.submit(**dict(stream[i][1], t_end=1e-13, tag=10**6 + i))
+        s.drain(len(shapes))
+        # capacity: runs one at a time
+        service = []
+        for i in range(n_capacity):
+            s.submit(**serving_kwargs(i, reqs[i][1]))
+            (r,) = s.drain(1)
+            service.append(r["run_s"])
+        cap = 1.0 / float(np.mean(service))
+        out["capacity_req_s"] = cap
+        out["capacity_sample"] = f"{n_capacity} requests run one at a time, mean service {np.mean(service):.3f} s"
+        levels = []
+        for load in loads:
+            rate = load * cap
+            st0 = s.stats()
+            t0 = time.perf_counter()
+            res = replay(s, stream, time_scale=1.0 / rate, timeout_s=900)
+            wall = time.perf_counter() - t0
+            st1 = s.stats()
+            ok = [r for r in res if r["status"] == 0]
+            lat = np.array([r["latency_s"] for r in ok])
+            ns = sum(nodes[r["tag"]] * r["n_accepted"] for r in ok)
+            levels.append({
+                "load": load, "rate_req_s": rate, "completed": len(ok), "failed": len(res) - len(ok),
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(lat.mean()), "max_s": float(lat.max()),
+                "mean_queue_s": float(np.mean([r["queue_s"] for r in ok])),
+                "throughput_req_s": len(ok) / wall, "node_steps_s": ns / wall, "wall_s": wall,
+                "busy_frac": (st1["busy_s"] - st0["busy_s"]) / wall,
+                "mean_active": (st1["active_s"] - st0["active_s"]) / wall,
+                "peak_active": st1["peak_active"], "peak_bytes": st1["peak_bytes"],
+                "meshes_created": st1["meshes_created"], "meshes_evicted": st1["meshes_evicted"]})
+        out["levels"] = levels
+    return out
 
 
 def main():
@@ -408,6 +476,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--serve-requests", type=int, default=40, help="requests per serving load level (0: skip)")
+    ap.add_argument("--serve-budget-gb", type=float, default=2.0)
+    ap.add_argument("--serve-max-active", type=int, default=16)
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -186,6 +186,86 @@ long nm_footprint_bytes(int n1, int n2, int n3, int precision);
 /* Block until all work enqueued on the mesh's stream has finished. */
 int nm_sync(nm_mesh mesh);
 
+/* ------------------------------------------------------------------------------------------------
+ * Serving: a request loop that runs many independent LLG integrations of different grid sizes and
+ * materials on one GPU.  The paper has no serving layer; each run is the single-mesh integration above
+ * (nm_run_until without samples) and its result is the same as that run alone.
+ *
+ * A server owns a worker thread and a pool of meshes.  Requests wait in a FIFO queue and are admitted
+ * when a slot is free (at most max_active runs at once) and their mesh fits the HBM budget: the sum of
+ * nm_footprint_bytes over the pooled meshes (running or idle) stays <= hbm_budget_bytes.  An idle mesh
+ * of the request's shape, cell size and precision is reused (its tensor spectrum stays resident);
+ * otherwise a mesh is created, with its tensor spectrum copied from a resident mesh of the same shape
+ * when there is one, and idle meshes of other shapes are destroyed, least recently used first, to make
+ * room.  Each admitted run keeps m and its RK state on the device and steps on its own stream in chunks
+ * of captured step graphs with device-side step control, so runs overlap on the device; the worker only
+ * reads each run's control block between chunks.  A request whose footprint exceeds the budget on its
+ * own completes with status NM_ERR_OOM.
+ * ------------------------------------------------------------------------------------------------ */
+typedef struct nm_server_s *nm_server;
+
+typedef struct {
+    int n[3];             /* cells N1 N2 N3 */
+    double dx[3];         /* cell size, m */
+    int precision;        /* NM_F32 | NM_F64 */
+    double Ms, A, Ku;     /* uniform material: A/m, J/m, J/m^3 */
+    double axis[3];       /* anisotropy axis (normalised by the library) */
+    double alpha, gamma;  /* damping; gyromagnetic ratio in m/(A s) */
+    double h[3];          /* uniform applied field, A/m */
+    unsigned terms;       /* NM_EXCH | NM_ANIS | NM_ZEE | NM_DEMAG */
+    int method;           /* NM_RK4 | NM_DP54 */
+    double t_end;         /* integrate from t = 0 to t_end, s */
+    double rtol, atol;    /* DP5 tolerances */
+    double dt0;           /* initial (RK4: fixed) step, s */
+    const double *m0;     /* HOST FP64 nodal vector field; borrowed until the request's result is returned */
+    double *m_out;        /* HOST FP64 nodal vector field receiving m(t_end), or NULL; borrowed likewise.
+                             Page-locked memory makes the copy asynchronous to the worker. */
+    long tag;             /* caller's identifier, echoed in the result */
+} nm_request;
+
+typedef struct {
+    long tag;
+    int status;                  /* NM_OK or the NM_ERR_* code of the failed run */
+    long n_accepted, n_rejected; /* step attempts of the run */
+    double t_final;              /* time reached */
+    double queue_s;              /* submit -> admission, s */
+    double run_s;                /* admission -> result ready, s */
+    double latency_s;            /* submit -> result ready, s */
+    int n_active_at_admit;       /* runs on the device when this one was admitted (itself included) */
+    char message[128];           /* error message of a failed run ("" on success) */
+} nm_result;
+
+typedef struct {
+    long submitted, completed, failed;
+    int queued, active, pooled;  /* waiting requests; running runs; meshes held (running + idle) */
+    int peak_active;
+    long bytes_in_use;           /* sum of the footprints of the pooled meshes */
+    long peak_bytes;
+    long meshes_created, meshes_evicted, tensor_copies;
+    double busy_s;               /* wall time with at least one run on the device */
+    double active_s;             /* integral of the number of running runs over wall time */
+    double wall_s;               /* since nm_server_create */
+} nm_server_stats;
+
+/* Start a server on the current CUDA device.  hbm_budget_bytes > 0; 1 <= max_active <= 256.
+ * Errors: NM_ERR_ARG, NM_ERR_CUDA. */
+int nm_server_create(long hbm_budget_bytes, int max_active, nm_server *out);
+
+/* Queue a request (validated on the host; NM_ERR_ARG for bad sizes, tolerances or pointers; the cell
+ * counts and limits of nm_create_mesh apply).  Thread-safe. */
+int nm_server_submit(nm_server server, const nm_request *req);
+
+/* Move up to max_results finished results into out (in completion order) and set *n_out; waits up to
+ * wait_s seconds for the first one when none is ready (0: do not wait).  Thread-safe. */
+int nm_server_poll(nm_server server, nm_result *out, int max_results, double wait_s, int *n_out);
+
+/* Counters and occupancy of the server.  Thread-safe. */
+int nm_server_stats_get(nm_server server, nm_server_stats *out);
+
+/* Finish every queued and running request, stop the worker and free all meshes.  Results not yet
+ * polled are dropped. */
+int nm_server_destroy(nm_server server);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *nm_last_error(void);
 

@@ -154,10 +154,11 @@ def random_problem(rng: np.random.Generator, n, dx=(2e-9, 2.5e-9, 3e-9), heterog
                    m0=m0, terms=terms)
 
 
-def serving_requests(n_requests: int = 500, seed: int = 0, rate_hz: float = 1.0):
+def serving_requests(n_requests: int = 500, seed: int = 0, rate_hz: float = 1.0, duration_scale: float = 1.0):
     """Poisson stream of LLG runs: grids N1,N2 in {64,128,256}, N3 in {1,2,4,8}; Ms ~ U[4e5,1.2e6],
     A ~ U[5e-12,2e-11], alpha ~ U[0.01,0.5], |mu0 h| ~ U[0,100] mT in a random direction, duration
-    ~ U[0.2,2] ns, m0 near-uniform plus noise.  Returns a list of (arrival_s, Problem)."""
+    ~ U[0.2,2] ns (times duration_scale), m0 near-uniform plus noise.  Returns a list of
+    (arrival_s, Problem) with m0 left out (see serving_m0) so that long streams stay small."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
@@ -168,13 +169,18 @@ def serving_requests(n_requests: int = 500, seed: int = 0, rate_hz: float = 1.0)
         A = rng.uniform(5e-12, 2e-11)
         alpha = rng.uniform(0.01, 0.5)
         h = unit_vector(rng) * rng.uniform(0, 100e-3) / MU0
-        T = rng.uniform(0.2e-9, 2e-9)
+        T = rng.uniform(0.2e-9, 2e-9) * duration_scale
         d = unit_vector(rng)
-        nodes = tuple(v + 1 for v in n)
-        m0 = d + 0.05 * rng.standard_normal(nodes + (3,))
-        m0 /= np.linalg.norm(m0, axis=-1, keepdims=True)
         p = Problem(f"request {i}", n, (3e-9, 3e-9, 3e-9), Ms, A, 0.0, (0, 0, 1), alpha,
-                    h_uniform=tuple(h), m0=m0, terms=EXCH | ZEE | DEMAG,
-                    extra=dict(t_end=T, rtol=1e-5, atol=1e-5, dt0=1e-14))
+                    h_uniform=tuple(h), m0=None, terms=EXCH | ZEE | DEMAG,
+                    extra=dict(t_end=T, rtol=1e-5, atol=1e-5, dt0=1e-14, m0_dir=tuple(d),
+                               m0_seed=int(rng.integers(0, 2**31))))
         out.append((t, p))
     return out
+
+
+def serving_m0(p: Problem) -> np.ndarray:
+    """Initial state of a serving request: its seeded direction plus 5 % Gaussian noise, normalised."""
+    rng = np.random.default_rng(p.extra["m0_seed"])
+    m0 = np.asarray(p.extra["m0_dir"]) + 0.05 * rng.standard_normal(p.nodes + (3,))
+    return m0 / np.linalg.norm(m0, axis=-1, keepdims=True)

@@ -49,6 +49,30 @@ def lib_path() -> str:
 # (name, restype, argtypes) for every entry point of include/nmgb.h
 _d, _i, _u, _l, _vp = ctypes.c_double, ctypes.c_int, ctypes.c_uint, ctypes.c_long, ctypes.c_void_p
 _Pd, _Pi, _Pl = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)
+
+
+class Request(ctypes.Structure):
+    """nm_request of include/nmgb.h."""
+    _fields_ = [("n", _i * 3), ("dx", _d * 3), ("precision", _i), ("Ms", _d), ("A", _d), ("Ku", _d),
+                ("axis", _d * 3), ("alpha", _d), ("gamma", _d), ("h", _d * 3), ("terms", _u), ("method", _i),
+                ("t_end", _d), ("rtol", _d), ("atol", _d), ("dt0", _d), ("m0", _Pd), ("m_out", _Pd),
+                ("tag", _l)]
+
+
+class Result(ctypes.Structure):
+    """nm_result of include/nmgb.h."""
+    _fields_ = [("tag", _l), ("status", _i), ("n_accepted", _l), ("n_rejected", _l), ("t_final", _d),
+                ("queue_s", _d), ("run_s", _d), ("latency_s", _d), ("n_active_at_admit", _i),
+                ("message", ctypes.c_char * 128)]
+
+
+class ServerStats(ctypes.Structure):
+    """nm_server_stats of include/nmgb.h."""
+    _fields_ = [("submitted", _l), ("completed", _l), ("failed", _l), ("queued", _i), ("active", _i),
+                ("pooled", _i), ("peak_active", _i), ("bytes_in_use", _l), ("peak_bytes", _l),
+                ("meshes_created", _l), ("meshes_evicted", _l), ("tensor_copies", _l), ("busy_s", _d),
+                ("active_s", _d), ("wall_s", _d)]
+
 SIGNATURES = [
     ("nm_create_mesh", _i, [_i, _i, _i, _d, _d, _d, _i, _vp, ctypes.POINTER(_vp)]),
     ("nm_destroy_mesh", _i, [_vp]),
@@ -69,6 +93,11 @@ SIGNATURES = [
     ("nm_adjoint_run", _i, [_vp, _i, _d, _d, _d, _d, _d, _Pd, _Pd, _i, _l, _Pd, _Pd, _Pd, _Pl]),
     ("nm_footprint_bytes", _l, [_i, _i, _i, _i]),
     ("nm_sync", _i, [_vp]),
+    ("nm_server_create", _i, [_l, _i, ctypes.POINTER(_vp)]),
+    ("nm_server_submit", _i, [_vp, ctypes.POINTER(Request)]),
+    ("nm_server_poll", _i, [_vp, ctypes.POINTER(Result), _i, _d, _Pi]),
+    ("nm_server_stats_get", _i, [_vp, ctypes.POINTER(ServerStats)]),
+    ("nm_server_destroy", _i, [_vp]),
     ("nm_last_error", ctypes.c_char_p, []),
 ]
 

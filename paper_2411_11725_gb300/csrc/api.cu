@@ -133,10 +133,15 @@ static void release(nm_mesh M)
     delete M;
 }
 
-extern "C" long nm_footprint_bytes(int n1, int n2, int n3, int precision)
+long mesh_footprint(int n1, int n2, int n3, int precision)
 {
     if (n1 < 1 || n2 < 1 || n3 < 1) return -1;
     return footprint(make_geom(n1, n2, n3), precision);
+}
+
+extern "C" long nm_footprint_bytes(int n1, int n2, int n3, int precision)
+{
+    return mesh_footprint(n1, n2, n3, precision);
 }
 
 extern "C" const char *nm_last_error(void) { return g_last_error.c_str(); }
@@ -145,6 +150,12 @@ extern "C" int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, do
                               void *cuda_stream, nm_mesh *out)
 {
     g_last_error.clear();
+    return create_mesh(n1, n2, n3, dx1, dx2, dx3, precision, cuda_stream, nullptr, out);
+}
+
+int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, void *cuda_stream,
+                nm_mesh tensor_src, nm_mesh *out)
+{
     if (!out) return fail(NM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n1 < 1 || n2 < 1 || n3 < 1) return fail(NM_ERR_ARG, "cell counts must be >= 1 (got %d %d %d)", n1, n2, n3);
@@ -215,11 +226,27 @@ extern "C" int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, do
     cudaMemsetAsync(M->S, 0, 3 * g.s_comp * 2 * rs, M->st);
     cudaMemsetAsync(M->MsH, 0, 3 * g.cs * rs, M->st);
     cudaMemsetAsync(M->ctl, 0, sizeof(StepCtl), M->st);
+    cudaError_t e;
+    if (tensor_src && tensor_src->prec == precision && tensor_src->g.P1 == g.P1 && tensor_src->g.P2 == g.P2 &&
+        tensor_src->g.P3 == g.P3 && tensor_src->g.N1 == n1 && tensor_src->g.N2 == n2 && tensor_src->g.N3 == n3 &&
+        tensor_src->dx[0] == dx1 && tensor_src->dx[1] == dx2 && tensor_src->dx[2] == dx3) {
+        // same shape, cell size and precision: the twiddles and the tensor spectrum are copied, not rebuilt
+        cudaMemcpyAsync(M->tw64, tensor_src->tw64, (size_t)(1 << g.twlg) * sizeof(Cx<double>),
+                        cudaMemcpyDeviceToDevice, M->st);
+        cudaMemcpyAsync(M->tw, tensor_src->tw, (size_t)(1 << g.twlg) * 2 * rs, cudaMemcpyDeviceToDevice, M->st);
+        cudaMemcpyAsync(M->Nk, tensor_src->Nk, 6 * g.t_comp * rs, cudaMemcpyDeviceToDevice, M->st);
+        e = cudaStreamSynchronize(M->st);
+        if (e != cudaSuccess) {
+            release(M);
+            return fail(NM_ERR_CUDA, "mesh set-up failed: %s", cudaGetErrorString(e));
+        }
+        *out = M;
+        return NM_OK;
+    }
     // twiddles (host, long double) and the tensor spectrum (device, FP64)
     std::vector<Cx<double>> tw64;
     fill_twiddles<double>(g.twlg, tw64);
     cudaMemcpyAsync(M->tw64, tw64.data(), tw64.size() * sizeof(Cx<double>), cudaMemcpyHostToDevice, M->st);
-    cudaError_t e;
     if (precision == NM_F64) {
         cudaMemcpyAsync(M->tw, tw64.data(), tw64.size() * sizeof(Cx<double>), cudaMemcpyHostToDevice, M->st);
         e = build_tensor_spectrum<double>(g, dx1, dx2, dx3, M->tw64, (double *)M->Nk, M->st);

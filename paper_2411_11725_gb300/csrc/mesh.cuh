@@ -103,6 +103,11 @@ struct nm_mesh_s {
 
 
 int dev_alloc(nm_mesh M, void **p, size_t bytes);
+// nm_create_mesh; with tensor_src a mesh of the same shape, cell size and precision, the twiddles and
+// the tensor spectrum are copied from it on the device instead of being rebuilt
+int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, void *cuda_stream,
+                nm_mesh tensor_src, nm_mesh *out);
+long mesh_footprint(int n1, int n2, int n3, int precision);
 int pull_ctl(nm_mesh M);
 int push_ctl(nm_mesh M);
 void free_graphs(nm_mesh M);

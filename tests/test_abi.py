@@ -62,3 +62,46 @@ def test_footprint_arithmetic(lib):
     # the largest throughput grid fits comfortably in one GB300's HBM
     assert big < 20e9 and f64 < 40e9
     assert lib.nm_footprint_bytes(0, 1, 1, 0) == -1
+
+
+def _request(nmgb, **kw):
+    import numpy as np
+    n = kw.pop("n", (8, 8, 2))
+    m0 = np.zeros((n[0] + 1, n[1] + 1, n[2] + 1, 3))
+    m0[..., 2] = 1
+    r = nmgb.Request()
+    r.n = (ctypes.c_int * 3)(*n)
+    r.dx = (ctypes.c_double * 3)(*kw.pop("dx", (3e-9, 3e-9, 3e-9)))
+    r.precision = kw.pop("precision", 0)
+    r.Ms, r.A, r.Ku = kw.pop("Ms", 8e5), 1.3e-11, 0.0
+    r.axis = (ctypes.c_double * 3)(0, 0, 1)
+    r.alpha, r.gamma = 0.1, 2.2e5
+    r.terms = kw.pop("terms", 13)
+    r.method = kw.pop("method", 2)
+    r.t_end = kw.pop("t_end", 1e-12)
+    r.rtol = r.atol = kw.pop("tol", 1e-5)
+    r.dt0 = kw.pop("dt0", 1e-14)
+    r.m0 = None if kw.pop("no_m0", False) else m0.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return r, m0
+
+
+def test_server_host_side_validation(lib):
+    """Request and server arguments are checked on the host before any CUDA call."""
+    import paper_2411_11725_gb300 as nmgb
+    h = ctypes.c_void_p()
+    assert lib.nm_server_create(0, 4, ctypes.byref(h)) == -1
+    assert lib.nm_server_create(1 << 30, 0, ctypes.byref(h)) == -1
+    assert lib.nm_server_create(1 << 30, 4, None) == -1
+    assert lib.nm_server_destroy(None) == 0
+    cases = [dict(n=(0, 8, 1)), dict(n=(2048, 8, 1)), dict(dx=(0, 1e-9, 1e-9)), dict(precision=3),
+             dict(Ms=-1.0), dict(terms=64), dict(method=7), dict(t_end=0.0), dict(dt0=-1.0), dict(tol=0.0),
+             dict(no_m0=True)]
+    for kw in cases:
+        r, _ = _request(nmgb, **kw)
+        assert lib.nm_server_submit(None, ctypes.byref(r)) == -1, kw
+        assert b"server is NULL" not in lib.nm_last_error(), kw
+    r, _ = _request(nmgb)
+    assert lib.nm_server_submit(None, ctypes.byref(r)) == -1
+    assert b"server is NULL" in lib.nm_last_error()
+    n = ctypes.c_int()
+    assert lib.nm_server_poll(None, None, 0, 0.0, ctypes.byref(n)) == -1
