@@ -153,6 +153,18 @@ int nm_run_until(nm_mesh mesh, double t_end, int method, double rtol, double ato
 int nm_profile_step(nm_mesh mesh, int method, int reps, double rtol, double atol, int max_kernels,
                     double *ms_out, char *names_out, int *n_kernels);
 
+/* As nm_get_state with where = NM_MEM_HOST, but allocating nothing: the node-major staging copy of m
+ * lives in a fixed 4 MiB device array of the library instead of a stream-ordered allocation.  The
+ * paper has no counterpart; this serves callers that cannot allocate device memory when they read a
+ * state back (a request loop whose HBM budget is fully committed to resident runs; a caller that keeps
+ * allocator calls out of its read-back path).  m_out: HOST FP64 nodal vector field (or NULL for t, dt
+ * only).  Limit: meshes of at most 174762 nodes (4 MiB / 24 B); larger meshes return NM_ERR_ARG.  The
+ * first call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
+ * call before any stream capture on that device.  Nothing in the array needs to start at zero.  The
+ * call synchronises the mesh's stream; calls on different meshes that overlap on the GPU (from several
+ * host threads) race on the shared array.  Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_CUDA. */
+int nm_get_state_noalloc(nm_mesh mesh, double *m_out, double *t, double *dt);
+
 /* Transpose product of the effective field (the gradient of <v, h_eff(m)>), for inverse problems
  * (section "Inverse Micromagnetics"; static problems differentiate the discretised field, the
  * discretise-first approach).  m, v: DEVICE real nodal vector fields; grad_m (DEVICE real nodal vector

@@ -80,6 +80,7 @@ SIGNATURES = [
     ("nm_set_field", _i, [_vp, _i, _Pd, _Pd, _d, _d]),
     ("nm_set_state", _i, [_vp, _vp, _i, _d, _d]),
     ("nm_get_state", _i, [_vp, _vp, _i, _Pd, _Pd]),
+    ("nm_get_state_noalloc", _i, [_vp, _Pd, _Pd, _Pd]),
     ("nm_set_integrator", _i, [_vp, _i, _d, _i]),
     ("nm_h_eff", _i, [_vp, _vp, _vp, _u, _d]),
     ("nm_set_terms", _i, [_vp, _u]),
