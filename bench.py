@@ -313,35 +313,39 @@ def run_ours(args, rank, world, dist):
     # per-launch timing for the roofline (CUDA events between launches on the mesh stream)
     prof = me.profile_step(nmgb.DP54, reps=3)
     # ---- e2e: the public API with host buffers, every step: H2D of m, one step, D2H of m
-    m_host = torch.from_numpy(m0.copy()).pin_memory()
-    out_host = torch.empty_like(m_host).pin_memory()
-    me.set_state(m_host.numpy(), 0.0, me.get_state()[2])
-    ke = max(2, min(K, args.e2e_steps))
-    torch.cuda.synchronize()
-    barrier()
-    t_e = time.perf_counter()
-    acc_e = 0
-    dt_e = me.get_state()[2]
-    for _ in range(ke):
-        me.set_state_host_ptr(m_host, 0.0, dt_e)
-        me.run_steps(1, nmgb.DP54, 1e-5, 1e-5)
-        _, dt_e = me.get_state_host_ptr(out_host)
-        acc_e += me.counters()[0]
-    torch.cuda.synchronize()
-    el_e = max_over_ranks(time.perf_counter() - t_e)
-    e2e_value = nn * sum_over_ranks(acc_e) / el_e
+    e2e_value, ke = None, 0
+    if args.e2e_steps > 0:
+        m_host = torch.from_numpy(m0.copy()).pin_memory()
+        out_host = torch.empty_like(m_host).pin_memory()
+        me.set_state(m_host.numpy(), 0.0, me.get_state()[2])
+        ke = max(2, min(K, args.e2e_steps))
+        torch.cuda.synchronize()
+        barrier()
+        t_e = time.perf_counter()
+        acc_e = 0
+        dt_e = me.get_state()[2]
+        for _ in range(ke):
+            me.set_state_host_ptr(m_host, 0.0, dt_e)
+            me.run_steps(1, nmgb.DP54, 1e-5, 1e-5)
+            _, dt_e = me.get_state_host_ptr(out_host)
+            acc_e += me.counters()[0]
+        torch.cuda.synchronize()
+        el_e = max_over_ranks(time.perf_counter() - t_e)
+        e2e_value = nn * sum_over_ranks(acc_e) / el_e
     me.close()
     del me
     # ---- plain FP64 path on the same workload (fewer steps: it is several times slower)
-    k64 = max(2, min(K, args.fp64_steps))
-    me = make(nmgb.F64)
-    me.run_steps(min(W, 3), nmgb.DP54, 1e-5, 1e-5)
-    me.sync()
-    ms64, acc64, _ = timed_steps(me, k64)
-    ms64 = max_over_ranks(ms64)
-    value64 = nn * sum_over_ranks(acc64) / (ms64 * 1e-3)
-    me.close()
-    del me
+    value64, ms64, k64 = None, None, 0
+    if args.fp64_steps > 0:
+        k64 = max(2, min(K, args.fp64_steps))
+        me = make(nmgb.F64)
+        me.run_steps(min(W, 3), nmgb.DP54, 1e-5, 1e-5)
+        me.sync()
+        ms64, acc64, _ = timed_steps(me, k64)
+        ms64 = max_over_ranks(ms64)
+        value64 = nn * sum_over_ranks(acc64) / (ms64 * 1e-3)
+        me.close()
+        del me
 
     if rank != 0:
         return
@@ -375,7 +379,9 @@ def run_ours(args, rank, world, dist):
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(args.serve_requests, int(args.serve_budget_gb * (1 << 30)), args.serve_max_active)
-    cpu_v, cores, cs_steps, cs_el, cs_desc = oracle_sample(seconds=args.cpu_seconds)
+    cpu_v, cores, cs_desc = None, None, "skipped (--cpu-seconds 0)"
+    if args.cpu_seconds > 0:
+        cpu_v, cores, cs_steps, cs_el, cs_desc = oracle_sample(seconds=args.cpu_seconds)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -386,8 +392,8 @@ def run_ours(args, rank, world, dist):
                    "error norm and step control", "l2": "working set larger than L2 (no flush needed)",
                    "accepted_steps": int(acc_tot), "rejected_steps": int(sum_over_ranks(rej)),
                    "parallelism": f"replicas x{world}"},
-        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64, "steps": k64,
-                 "fp32_over_fp64": value / value64},
+        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64 if k64 else None, "steps": k64,
+                 "fp32_over_fp64": value / value64 if value64 else None},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(24 * nn),
                 "d2h_bytes_per_step": int(24 * nn), "steps": ke,
                 "note": "per step: nm_set_state from pinned host m, one DP5 step (FSAL slope recomputed), "

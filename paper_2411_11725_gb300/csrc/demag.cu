@@ -4,172 +4,252 @@
 // fuses forward y, the product and inverse y), and a pruned complex-to-real x transform that writes
 // Ms_c H_c per cell.
 //
-// The x passes read their input in the first FFT stage straight from global memory (the zero padding
-// is never read); the y and z passes stage their strided tiles in shared memory with cp.async (all
-// copies of a tile in flight at once).  Every pass writes its output from the last FFT stage straight
-// to global memory, and only the part that later passes read.
+// Every kernel is instantiated per log2 transform length (the f3 engine), so the index arithmetic of
+// the FFT stages is resolved at compile time.  The x passes read their input in the first FFT stage
+// straight from global memory (the zero padding is never read); the y and z passes stage their strided
+// tiles in shared memory with cp.async (all copies of a tile in flight at once).  Every pass writes its
+// output from the last FFT stage straight to global memory, and only the part that later passes read.
 #include "demag.cuh"
-#include "fft.cuh"
+#include "fft3.cuh"
 
 namespace nm {
 
-constexpr int kFftThreads = 256;
-
-// ---------------------------------------------------------------------------------------------
-// node -> cell average times Ms for the cell pair (x, x+1) of one cell row:
-// M_c = Ms_c * (1/8) sum_{i in {0,1}^3} y_{c+i}
+constexpr int kXThreads = 256;
 template <typename T>
-__device__ __forceinline__ Cx<T> cell_M_pair(const Geom &g, const DemagBufs<T> &b, const T *__restrict__ yc,
-                                             long r00, long c0, int x)
+constexpr int kMaxThreads = sizeof(T) == 4 ? 1024 : 512;
+
+// Asynchronous global -> shared copies (cp.async): many in flight per thread without registers.
+__device__ __forceinline__ void cpa16(void *sm, const void *gm)
 {
-    const long r01 = r00 + g.nn1;
-    const long r10 = r00 + (long)g.nn2 * g.nn1;
-    const long r11 = r10 + g.nn1;
-    const T a0 = (yc[r00] + yc[r01]) + (yc[r10] + yc[r11]);
-    const T a1 = (yc[r00 + 1] + yc[r01 + 1]) + (yc[r10 + 1] + yc[r11 + 1]);
-    const T Ms0 = b.Ms ? b.Ms[c0] : b.Ms0;
-    T m0 = Ms0 * T(0.125) * (a0 + a1), m1 = T(0);
-    if (x + 1 < g.N1) {
-        const T a2 = (yc[r00 + 2] + yc[r01 + 2]) + (yc[r10 + 2] + yc[r11 + 2]);
-        const T Ms1 = b.Ms ? b.Ms[c0 + 1] : b.Ms0;
-        m1 = Ms1 * T(0.125) * (a1 + a2);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((unsigned)__cvta_generic_to_shared(sm)),
+                 "l"(gm)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa8(void *sm, const void *gm)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"((unsigned)__cvta_generic_to_shared(sm)),
+                 "l"(gm)
+                 : "memory");
+}
+__device__ __forceinline__ void cpa_wait_all()
+{
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+// copy `bytes` (a multiple of 8; both addresses aligned to min(bytes, 16)) as copy number ch of a row
+__device__ __forceinline__ void cpa_chunk(void *sm, const void *gm, int cb)
+{
+    if (cb == 16) cpa16(sm, gm);
+    else cpa8(sm, gm);
+}
+
+// x-pass line L = c * (N2 N3) + row, row = zz * N2 + yy: consecutive lines of a block are consecutive
+// cell rows of one component, so the node rows they average overlap.  Offsets (elements, int32: every
+// supported size fits) of the line's start in the node array, the cell arrays and the spectrum.
+struct XInfo {
+    int in;    // node array (nodal input) or cell array (cell input / output), component included
+    int cell;  // cell index of the row start (Ms map)
+    int spec;  // spectrum row start
+};
+__device__ __forceinline__ XInfo x_info(const Geom &g, const FastDiv &nrf, int L, bool cell_in)
+{
+    const int NR = g.N2 * g.N3;
+    const int c = (int)nrf.div((unsigned)L);
+    const int row = L - c * NR;
+    const int zz = (int)g.n2f.div((unsigned)row);
+    const int yy = row - zz * g.N2;
+    XInfo x;
+    x.cell = row * g.N1;
+    x.in = cell_in ? c * (int)g.cs + x.cell : c * (int)g.ns + (zz * g.nn2 + yy) * g.nn1;
+    x.spec = c * (int)g.s_comp + (zz * g.P2 + yy) * g.Xp;
+    return x;
+}
+
+// M of the cell pair (x, x+1) of a row: M_c = Ms_c * (1/8) sum_{i in {0,1}^3} y_{c+i}.  p points at node
+// (x, yy, zz) of one component.
+template <typename T>
+__device__ __forceinline__ Cx<T> cell_M_pair(const T *__restrict__ p, int nn1, int plane, const T *__restrict__ Ms,
+                                             T Ms0, int cell, bool has2)
+{
+    const T a0 = (p[0] + p[nn1]) + (p[plane] + p[plane + nn1]);
+    const T a1 = (p[1] + p[nn1 + 1]) + (p[plane + 1] + p[plane + nn1 + 1]);
+    const T ms0 = Ms ? Ms[cell] : Ms0;
+    T m0 = ms0 * T(0.125) * (a0 + a1), m1 = T(0);
+    if (has2) {
+        const T a2 = (p[2] + p[nn1 + 2]) + (p[plane + 2] + p[plane + nn1 + 2]);
+        const T ms1 = Ms ? Ms[cell + 1] : Ms0;
+        m1 = ms1 * T(0.125) * (a1 + a2);
     }
     return cx<T>(m0, m1);
 }
 
-// Line L of the x passes is (cell row, component) = (L / 3, L % 3); cell row = zz * N2 + yy.
-struct XLine {
-    int c, yy, zz, row;
-};
-__device__ __forceinline__ XLine x_line(const Geom &g, int L)
-{
-    XLine x;
-    x.row = L / 3;
-    x.c = L - 3 * x.row;
-    x.zz = (int)g.n2f.div((unsigned)x.row);
-    x.yy = x.row - x.zz * g.N2;
-    return x;
-}
-
-// Pass 1: x transform (R2C of length P1 via a complex FFT of length Q = P1/2 on even/odd pairs).
+// Pass 1: x transform (R2C of length P1 = 2Q via a complex FFT of length Q = 2^LG on even/odd pairs).
 // One block holds `lpb` consecutive lines.  CELL_IN: the input is already a cell field.
-template <typename T, bool CELL_IN>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_x_fwd(Geom g, DemagBufs<T> b, const T *__restrict__ in, int lpb)
+template <typename T, bool CELL_IN, int LG>
+__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 3 : 2)
+    k_x_fwd(Geom g, DemagBufs<T> b, const T *__restrict__ in, int lpb)
 {
     if (b.ctl && b.ctl->done) return;
+    constexpr int Q = 1 << LG, H = Q / 2, LSZ = f3::padded(Q);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
+    XInfo *info = reinterpret_cast<XInfo *>(buf + lpb * LSZ);
     const int nlines = 3 * g.N2 * g.N3;
     const int l0 = blockIdx.x * lpb;
     const int nl = min(lpb, nlines - l0);
     if (nl <= 0) return;
-    auto pair = [&](const XLine &xl, int x) -> Cx<T> {
-        const long c0 = (long)xl.row * g.N1 + x;
-        if (CELL_IN) {
-            const T *p = in + xl.c * g.cs + c0;
-            return cx<T>(p[0], x + 1 < g.N1 ? p[1] : T(0));
-        }
-        const long r00 = ((long)xl.zz * g.nn2 + xl.yy) * g.nn1 + x;
-        return cell_M_pair(g, b, in + xl.c * g.ns, r00, c0, x);
+    if (threadIdx.x < nl) info[threadIdx.x] = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), l0 + threadIdx.x, CELL_IN);
+    __syncthreads();
+    const int N1 = g.N1, nn1 = g.nn1, plane = g.nn2 * g.nn1;
+    const T *Ms = b.Ms;
+    const T Ms0 = b.Ms0;
+    auto src = [&](int l, int i) -> Cx<T> {
+        const int x = 2 * i;
+        const XInfo xi = info[l];
+        const T *p = in + xi.in + x;
+        if (CELL_IN) return cx<T>(p[0], x + 1 < N1 ? p[1] : T(0));
+        return cell_M_pair<T>(p, nn1, plane, Ms, Ms0, xi.cell + x, x + 1 < N1);
     };
-    if (g.P1 == 1) {
-        for (int t = threadIdx.x; t < nl; t += blockDim.x) {
-            const XLine xl = x_line(g, l0 + t);
-            b.S[xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp] = cx<T>(pair(xl, 0).x, T(0));
-        }
-        return;
-    }
-    const int Q = g.Q, lsz = padded_len(Q);
-    auto src = [&](int l, int i) -> Cx<T> { return pair(x_line(g, l0 + l), 2 * i); };
-    auto sm = [&](int l, int i) { return l * lsz + pad16(i); };
-    auto dst = [&](int l, int i, Cx<T> v) { buf[l * lsz + pad16(i)] = v; };
-    fft_lines<T, false, false, true>(buf, FastDiv((unsigned)nl), g.lgQ, -1, b.tw, g.twlg, (g.N1 + 1) >> 1, Q, src,
-                                     sm, dst);
-    // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}),  W = e^{-2 pi i / P1},  k = 0..Q
-    const int wsh = g.twlg - (g.lgQ + 1);
-    const FastDiv qf((unsigned)(Q + 1));
-    for (int t = threadIdx.x; t < nl * (Q + 1); t += blockDim.x) {
-        const int l = (int)qf.div((unsigned)t), k = t - l * (Q + 1);
-        const XLine xl = x_line(g, l0 + l);
-        const Cx<T> Zk = buf[l * lsz + pad16(k == Q ? 0 : k)];
-        const Cx<T> Zc = conj(buf[l * lsz + pad16(k == 0 ? 0 : Q - k)]);
+    f3::fft<T, LG, -1, false, false, true>(buf, nl, FastDiv(1u), b.tw, g.twlg, (N1 + 1) >> 1, Q, src, f3::NoFn<T>());
+    // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}),  W = e^{-2 pi i / P1},  k = 0..Q;
+    // thread (l, k) with k < Q/2 writes X_k and X_{Q-k}; k = 0 also writes X_{Q/2} (and X_0, X_Q)
+    const int wsh = g.twlg - (LG + 1);
+    const Cx<T> *tw = b.tw;
+    auto xk = [&](Cx<T> Zk, Cx<T> Zq, int k) -> Cx<T> {
+        const Cx<T> Zc = conj(Zq);
         const Cx<T> E = scale(Zk + Zc, T(0.5));
         const Cx<T> O = scale(mul_si(Zk - Zc, -1), T(0.5));
-        b.S[xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp + k] = E + b.tw[k << wsh] * O;
+        return E + tw[k << wsh] * O;
+    };
+    for (int t = threadIdx.x; t < nl * H; t += blockDim.x) {
+        const int l = t >> (LG - 1 < 0 ? 0 : LG - 1), k = t & (H - 1);
+        const Cx<T> *z = buf + l * LSZ;
+        Cx<T> *out = b.S + info[l].spec;
+        if (k == 0) {
+            const Cx<T> Z0 = z[0];
+            out[0] = xk(Z0, Z0, 0);
+            out[Q] = xk(Z0, Z0, Q);
+            if (H > 0 && Q > 1) {
+                const Cx<T> Zh = z[f3::pad16c(H)];
+                out[H] = xk(Zh, Zh, H);
+            }
+        } else {
+            const Cx<T> Zk = z[f3::pad16c(k)], Zq = z[f3::pad16c(Q - k)];
+            out[k] = xk(Zk, Zq, k);
+            out[Q - k] = xk(Zq, Zk, Q - k);
+        }
     }
+}
+
+// N1 == 1 (P1 == 1): the x "transform" is a copy of the cell value (real) into kx = 0.
+template <typename T, bool CELL_IN>
+__global__ void k_x_fwd1(Geom g, DemagBufs<T> b, const T *__restrict__ in)
+{
+    if (b.ctl && b.ctl->done) return;
+    const int nlines = 3 * g.N2 * g.N3;
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nlines) return;
+    const XInfo xi = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), L, CELL_IN);
+    T v;
+    if (CELL_IN) v = in[xi.in];
+    else v = cell_M_pair<T>(in + xi.in, g.nn1, g.nn2 * g.nn1, b.Ms, b.Ms0, xi.cell, false).x;
+    b.S[xi.spec] = cx<T>(v, T(0));
 }
 
 // Pass 5: inverse x transform (C2R of length P1 via a complex FFT of length Q), keeping x < N1.
-// Lines as in pass 1.  Output per cell: Ms_c H_c (or H_c when CELL_OUT).
-template <typename T, bool CELL_OUT>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_x_inv(Geom g, DemagBufs<T> b, T *__restrict__ out, int lpb)
+// Output per cell: Ms_c H_c (or H_c when CELL_OUT).
+template <typename T, bool CELL_OUT, int LG>
+__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 3 : 2)
+    k_x_inv(Geom g, DemagBufs<T> b, T *__restrict__ out, int lpb)
 {
     if (b.ctl && b.ctl->done) return;
+    constexpr int Q = 1 << LG, H = Q / 2, LSZ = f3::padded(Q);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
+    XInfo *info = reinterpret_cast<XInfo *>(buf + lpb * LSZ);
     const int nlines = 3 * g.N2 * g.N3;
     const int l0 = blockIdx.x * lpb;
     const int nl = min(lpb, nlines - l0);
     if (nl <= 0) return;
-    auto put = [&](int c, long cell, T v) {
-        if (!CELL_OUT) v *= b.Ms ? b.Ms[cell] : b.Ms0;
-        out[c * g.cs + cell] = v;
+    if (threadIdx.x < nl) info[threadIdx.x] = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), l0 + threadIdx.x, true);
+    __syncthreads();
+    // Z_k = (X_k + conj X_{Q-k}) + i conj(W^k) (X_k - conj X_{Q-k}), k < Q, into shared memory
+    const int wsh = g.twlg - (LG + 1);
+    const Cx<T> *tw = b.tw;
+    auto zk = [&](Cx<T> Xk, Cx<T> Xq, int k) -> Cx<T> {
+        const Cx<T> Xc = conj(Xq);
+        return (Xk + Xc) + mul_si((Xk - Xc) * conj(tw[k << wsh]), 1);
     };
-    if (g.P1 == 1) {
-        for (int t = threadIdx.x; t < nl; t += blockDim.x) {
-            const XLine xl = x_line(g, l0 + t);
-            put(xl.c, (long)xl.row * g.N1, b.S[xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp].x);
+    for (int t = threadIdx.x; t < nl * H; t += blockDim.x) {
+        const int l = t >> (LG - 1 < 0 ? 0 : LG - 1), k = t & (H - 1);
+        const Cx<T> *s = b.S + info[l].spec;
+        Cx<T> *z = buf + l * LSZ;
+        if (k == 0) {
+            z[0] = zk(s[0], s[Q], 0);
+            if (H > 0 && Q > 1) {
+                const Cx<T> Xh = s[H];
+                z[f3::pad16c(H)] = zk(Xh, Xh, H);
+            }
+        } else {
+            const Cx<T> Xk = s[k], Xq = s[Q - k];
+            z[f3::pad16c(k)] = zk(Xk, Xq, k);
+            z[f3::pad16c(Q - k)] = zk(Xq, Xk, Q - k);
         }
-        return;
     }
-    const int Q = g.Q, lsz = padded_len(Q);
-    const int wsh = g.twlg - (g.lgQ + 1);
-    // Z_k = (X_k + conj X_{Q-k}) + i e^{2 pi i k / P1} (X_k - conj X_{Q-k}), k < Q
-    auto src = [&](int l, int k) -> Cx<T> {
-        const XLine xl = x_line(g, l0 + l);
-        const Cx<T> *s = b.S + xl.c * g.s_comp + ((long)xl.zz * g.P2 + xl.yy) * g.Xp;
-        const Cx<T> Xk = s[k], Xc = conj(s[Q - k]);
-        return (Xk + Xc) + mul_si((Xk - Xc) * conj(b.tw[k << wsh]), 1);
-    };
-    auto sm = [&](int l, int i) { return l * lsz + pad16(i); };
+    __syncthreads();
+    const int N1 = g.N1;
+    const T *Ms = b.Ms;
+    const T Ms0 = b.Ms0;
     auto dst = [&](int l, int j, Cx<T> v) {
-        const XLine xl = x_line(g, l0 + l);
-        const long cell = (long)xl.row * g.N1 + 2 * j;
-        put(xl.c, cell, v.x);
-        if (2 * j + 1 < g.N1) put(xl.c, cell + 1, v.y);
+        const XInfo xi = info[l];
+        const int x = 2 * j;
+        T v0 = v.x, v1 = v.y;
+        if (!CELL_OUT) {
+            v0 *= Ms ? Ms[xi.cell + x] : Ms0;
+            if (x + 1 < N1) v1 *= Ms ? Ms[xi.cell + x + 1] : Ms0;
+        }
+        out[xi.in + x] = v0;
+        if (x + 1 < N1) out[xi.in + x + 1] = v1;
     };
-    fft_lines<T, false, false, false>(buf, FastDiv((unsigned)nl), g.lgQ, +1, b.tw, g.twlg, Q, (g.N1 + 1) >> 1, src,
-                                      sm, dst);
+    f3::fft<T, LG, +1, false, true, false>(buf, nl, FastDiv(1u), b.tw, g.twlg, Q, (N1 + 1) >> 1, f3::NoFn<T>(), dst);
+}
+
+template <typename T, bool CELL_OUT>
+__global__ void k_x_inv1(Geom g, DemagBufs<T> b, T *__restrict__ out)
+{
+    if (b.ctl && b.ctl->done) return;
+    const int nlines = 3 * g.N2 * g.N3;
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nlines) return;
+    const XInfo xi = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), L, true);
+    T v = b.S[xi.spec].x;
+    if (!CELL_OUT) v *= b.Ms ? b.Ms[xi.cell] : b.Ms0;
+    out[xi.in] = v;
 }
 
 // Passes 2 and 4: y transform of G consecutive kx columns of one (component, z) plane, in place.
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
-// The rows are staged with cp.async (all in flight at once), the last stage writes global memory.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_y(Geom g, DemagBufs<T> b, int G, int dir)
+// Shared layout: row y at buf + y * G (lines = columns, fastest).
+template <typename T, int LG, int DIR>
+__global__ void __launch_bounds__(kMaxThreads<T>, 1) k_y(Geom g, DemagBufs<T> b, int G)
 {
     if (b.ctl && b.ctl->done) return;
+    constexpr int P2 = 1 << LG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *base = b.S + (long)blockIdx.y * g.P2 * g.Xp + blockIdx.x * G;
-    const int nin = dir < 0 ? g.N2 : g.P2, nout = dir < 0 ? g.P2 : g.N2;
+    Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
+    const int nin = DIR < 0 ? g.N2 : P2, nout = DIR < 0 ? P2 : g.N2;
     const int Xp = g.Xp;
     const int rowb = G * (int)sizeof(Cx<T>);
-    const int cb = rowb >= 16 ? 16 : rowb;  // bytes per async copy
+    const int cb = rowb >= 16 ? 16 : rowb;
     const int lcpr = __ffs(rowb / cb) - 1;  // copies per row is a power of two
     for (int t = threadIdx.x; t < (nin << lcpr); t += blockDim.x) {
         const int y = t >> lcpr, ch = t - (y << lcpr);
-        char *d = (char *)(buf + pad16(y) * G) + ch * cb;
-        const char *s = (const char *)(base + y * Xp) + ch * cb;
-        if (cb == 16) cp_async16(d, s);
-        else cp_async8(d, s);
+        cpa_chunk((char *)(buf + y * G) + ch * cb, (const char *)(base + y * Xp) + ch * cb, cb);
     }
-    cp_async_wait_all();
+    cpa_wait_all();
     __syncthreads();
-    auto sm = [&](int l, int i) { return pad16(i) * G + l; };
-    auto sm_src = [&](int l, int i) { return buf[pad16(i) * G + l]; };
     auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    fft_lines<T, true, true, false>(buf, FastDiv((unsigned)G), g.lgP2, dir, b.tw, g.twlg, nin, nout, sm_src, sm, dst);
+    f3::fft<T, LG, DIR, true, true, false>(buf, G, FastDiv((unsigned)G), b.tw, g.twlg, nin, nout, f3::NoFn<T>(), dst);
 }
 
 // The six real tensor components at octant frequency (kx, a2, kz), with the sign of the odd ones in
@@ -205,11 +285,12 @@ __device__ __forceinline__ void tensor_mul(const Ten6<T> &t, T s2, Cx<T> *px, Cx
 // Pass 3 (N3 > 1): G kx columns x KY octant rows a2 (each with its mirror P2 - a2, so the tensor is
 // read once): forward z (N3 non-zero inputs), tensor product, inverse z keeping z < N3.
 // Rows r < KY are ky = a2_0 + r, rows KY + r are ky = P2 - (a2_0 + r) (present when 0 < a2 < P2/2).
-// Lines l = (c * 2KY + r) * G + g, innermost in shared memory.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
+// Lines l = (c * 2KY + r) * G + g; element kz of line l at buf[kz * nl + l].
+template <typename T, int LG>
+__global__ void __launch_bounds__(kMaxThreads<T>, 1) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
 {
     if (b.ctl && b.ctl->done) return;
+    constexpr int P3 = 1 << LG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
@@ -221,9 +302,7 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_z_conv(
         if (r < KY) return a2;
         return (a2 > 0 && a2 < h2) ? g.P2 - a2 : -1;
     };
-    auto gaddr = [&](int c, int ky, int z) -> long {
-        return c * g.s_comp + ((long)z * g.P2 + ky) * g.Xp + kx0;
-    };
+    auto gaddr = [&](int c, int ky, int z) -> long { return c * g.s_comp + ((long)z * g.P2 + ky) * g.Xp + kx0; };
     {
         const int rowb = G * (int)sizeof(Cx<T>);
         const int cb = rowb >= 16 ? 16 : rowb, lcpr = __ffs(rowb / cb) - 1, lR2 = __ffs(R2) - 1;
@@ -233,27 +312,22 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_z_conv(
             const int r = rr & (R2 - 1), cz = rr >> lR2, z = cz / 3, c = cz - 3 * z;
             const int ky = row_ky(r);
             if (ky < 0) continue;
-            char *d = (char *)(buf + pad16(z) * nl + (c * R2 + r) * G) + ch * cb;
-            const char *s = (const char *)(b.S + gaddr(c, ky, z)) + ch * cb;
-            if (cb == 16) cp_async16(d, s);
-            else cp_async8(d, s);
+            cpa_chunk((char *)(buf + z * nl + (c * R2 + r) * G) + ch * cb, (const char *)(b.S + gaddr(c, ky, z)) + ch * cb,
+                      cb);
         }
-        cp_async_wait_all();
+        cpa_wait_all();
         __syncthreads();
     }
     const FastDiv nlf((unsigned)nl);
-    auto sm = [&](int l, int i) { return pad16(i) * nl + l; };
-    auto sm_src = [&](int l, int i) { return buf[pad16(i) * nl + l]; };
-    auto sm_dst = [&](int l, int i, Cx<T> v) { buf[pad16(i) * nl + l] = v; };
-    fft_lines<T, true, true, true>(buf, nlf, g.lgP3, -1, b.tw, g.twlg, g.N3, g.P3, sm_src, sm, sm_dst);
-    const int npts = KY * G * g.P3;
+    f3::fft<T, LG, -1, true, true, true>(buf, nl, nlf, b.tw, g.twlg, g.N3, P3, f3::NoFn<T>(), f3::NoFn<T>());
+    const int npts = KY * G * P3;
     const int lG = __ffs(G) - 1, lKY = __ffs(KY) - 1;
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
         const int gg = t & (G - 1), q = t >> lG, rr = q & (KY - 1), kz = q >> lKY;
         const int a2 = a20 + rr;
         if (a2 >= g.H2) continue;
         const Ten6<T> ten = tensor_at(g, b, kx0 + gg, a2, kz);
-        Cx<T> *p = buf + pad16(kz) * nl + rr * G + gg;
+        Cx<T> *p = buf + kz * nl + rr * G + gg;
         tensor_mul(ten, T(1), p, p + R2 * G, p + 2 * R2 * G);
         if (a2 > 0 && a2 < h2) {
             Cx<T> *pm = p + KY * G;
@@ -266,20 +340,22 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_z_conv(
         const int ky = row_ky(r);
         if (ky >= 0) b.S[gaddr(c, ky, z) + gg] = v;
     };
-    fft_lines<T, true, true, false>(buf, nlf, g.lgP3, +1, b.tw, g.twlg, g.P3, g.N3, sm_src, sm, dst);
+    f3::fft<T, LG, +1, true, true, false>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
 }
 
 // Single-layer variant (N3 == 1, P3 == 1): forward y, tensor product at kz = 0 (each octant row a2
-// read once and applied to ky = a2 and P2 - a2), inverse y.  Lines l = c * G + g.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_y_conv(Geom g, DemagBufs<T> b, int G)
+// read once and applied to ky = a2 and P2 - a2), inverse y.  Lines l = c * G + g; element y of line l
+// at buf[y * nl + l].  LG = 0 (N2 == 1): the product alone.
+template <typename T, int LG>
+__global__ void __launch_bounds__(kMaxThreads<T>, 1) k_y_conv(Geom g, DemagBufs<T> b, int G)
 {
     if (b.ctl && b.ctl->done) return;
+    constexpr int P2 = 1 << LG;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G;
     const int nl = 3 * G;
-    const int h2 = g.P2 >> 1;
+    const int h2 = P2 >> 1;
     auto gaddr = [&](int c, int y) -> long { return c * g.s_comp + (long)y * g.Xp + kx0; };
     {
         const int rowb = G * (int)sizeof(Cx<T>);
@@ -288,27 +364,22 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_y_conv(
         for (int t = threadIdx.x; t < (nrow << lcpr); t += blockDim.x) {
             const int rr = t >> lcpr, ch = t - (rr << lcpr);
             const int y = rr / 3, c = rr - 3 * y;
-            char *d = (char *)(buf + pad16(y) * nl + c * G) + ch * cb;
-            const char *s = (const char *)(b.S + gaddr(c, y)) + ch * cb;
-            if (cb == 16) cp_async16(d, s);
-            else cp_async8(d, s);
+            cpa_chunk((char *)(buf + y * nl + c * G) + ch * cb, (const char *)(b.S + gaddr(c, y)) + ch * cb, cb);
         }
-        cp_async_wait_all();
+        cpa_wait_all();
         __syncthreads();
     }
     const FastDiv nlf((unsigned)nl);
-    auto sm = [&](int l, int i) { return pad16(i) * nl + l; };
-    auto sm_src = [&](int l, int i) { return buf[pad16(i) * nl + l]; };
-    auto sm_dst = [&](int l, int i, Cx<T> v) { buf[pad16(i) * nl + l] = v; };
-    fft_lines<T, true, true, true>(buf, nlf, g.lgP2, -1, b.tw, g.twlg, g.N2, g.P2, sm_src, sm, sm_dst);
+    if constexpr (LG > 0)
+        f3::fft<T, LG, -1, true, true, true>(buf, nl, nlf, b.tw, g.twlg, g.N2, P2, f3::NoFn<T>(), f3::NoFn<T>());
     const int lG = __ffs(G) - 1;
     for (int t = threadIdx.x; t < G * g.H2; t += blockDim.x) {
         const int gg = t & (G - 1), a2 = t >> lG;
         const Ten6<T> ten = tensor_at(g, b, kx0 + gg, a2, 0);
-        Cx<T> *p = buf + pad16(a2) * nl + gg;
+        Cx<T> *p = buf + a2 * nl + gg;
         tensor_mul(ten, T(1), p, p + G, p + 2 * G);
         if (a2 > 0 && a2 < h2) {
-            Cx<T> *pm = buf + pad16(g.P2 - a2) * nl + gg;
+            Cx<T> *pm = buf + (P2 - a2) * nl + gg;
             tensor_mul(ten, T(-1), pm, pm + G, pm + 2 * G);
         }
     }
@@ -317,76 +388,111 @@ __global__ void __launch_bounds__(kFftThreads, sizeof(T) == 4 ? 2 : 1) k_y_conv(
         const int gg = l & (G - 1), c = l >> lG;
         b.S[gaddr(c, y) + gg] = v;
     };
-    fft_lines<T, true, true, false>(buf, nlf, g.lgP2, +1, b.tw, g.twlg, g.P2, g.N2, sm_src, sm, dst);
+    if constexpr (LG > 0) {
+        f3::fft<T, LG, +1, true, true, false>(buf, nl, nlf, b.tw, g.twlg, P2, g.N2, f3::NoFn<T>(), dst);
+    } else {
+        for (int l = threadIdx.x; l < nl; l += blockDim.x) dst(l, 0, buf[l]);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
+static void set_smem(const void *f) { cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); }
+
+template <typename T>
+static void init_attributes_t()
+{
+    f3::lg_for_each<1, 10>([&](auto c) {
+        constexpr int LG = decltype(c)::value;
+        set_smem((const void *)k_x_fwd<T, false, LG>);
+        set_smem((const void *)k_x_fwd<T, true, LG>);
+        set_smem((const void *)k_x_inv<T, false, LG>);
+        set_smem((const void *)k_x_inv<T, true, LG>);
+    });
+    f3::lg_for_each<1, 11>([&](auto c) {
+        constexpr int LG = decltype(c)::value;
+        set_smem((const void *)k_y<T, LG, -1>);
+        set_smem((const void *)k_y<T, LG, +1>);
+    });
+    f3::lg_for_each<1, 7>([&](auto c) {
+        constexpr int LG = decltype(c)::value;
+        set_smem((const void *)k_z_conv<T, LG>);
+    });
+    f3::lg_for_each<0, 11>([&](auto c) {
+        constexpr int LG = decltype(c)::value;
+        set_smem((const void *)k_y_conv<T, LG>);
+    });
+}
+
 void demag_init_attributes()
 {
     static bool done = false;
     if (done) return;
-    const int lim = 200 * 1024;
-    const void *fns[] = {(const void *)k_x_fwd<float, false>, (const void *)k_x_fwd<float, true>,
-                         (const void *)k_x_fwd<double, false>, (const void *)k_x_fwd<double, true>,
-                         (const void *)k_x_inv<float, false>, (const void *)k_x_inv<float, true>,
-                         (const void *)k_x_inv<double, false>, (const void *)k_x_inv<double, true>,
-                         (const void *)k_y<float>, (const void *)k_y<double>,
-                         (const void *)k_z_conv<float>, (const void *)k_z_conv<double>,
-                         (const void *)k_y_conv<float>, (const void *)k_y_conv<double>};
-    for (const void *f : fns) cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    init_attributes_t<float>();
+    init_attributes_t<double>();
     done = true;
 }
 
 static int pow2_floor(long v)
 {
+    if (v < 1) return 0;
     int p = 1;
     while (2L * p <= v) p *= 2;
     return p;
 }
+static int threads_for(long elems)
+{
+    long t = (elems + 7) / 8;
+    t = t < 32 ? 32 : t;
+    return (int)((t + 31) / 32 * 32);
+}
 
-// Launch shapes: every block transforms at most fft_regs<T>() * kFftThreads complex values.
+// Launch shapes: every block transforms at most 8 complex values per thread; the y and z passes take
+// up to kMaxThreads<T> threads so that their rows span at least 64 bytes where the size allows.
 template <typename T>
 DemagPlan demag_plan(const Geom &g)
 {
     DemagPlan p{};
     p.ok = true;
     const size_t cs = sizeof(Cx<T>);
-    const long budget = (long)fft_regs<T>() * kFftThreads;
-    const int nlines = 3 * g.N2 * g.N3;
-    {
-        const int Q = g.P1 == 1 ? 1 : g.Q;
-        int lpb = (int)(budget / Q);
-        if (lpb < 1) p.ok = false;
-        lpb = lpb < 1 ? 1 : lpb;
-        lpb = lpb > 48 ? 48 : lpb;
-        lpb = lpb > nlines ? nlines : lpb;
-        p.x_lpb = lpb;
-        p.x_threads = kFftThreads;
-        p.x_smem = g.P1 == 1 ? 0 : (size_t)lpb * padded_len(Q) * cs;
+    const long budget = 8L * kMaxThreads<T>;
+    const int Gmin = (int)(64 / cs);
+    if (g.P1 > 1) {
+        int lpb = (int)(8L * kXThreads / g.Q);
+        lpb = lpb > 64 ? 64 : lpb;
+        if (lpb < 1 || g.lgQ > 10) p.ok = false;
+        p.x_lpb = lpb < 1 ? 1 : lpb;
+        p.x_threads = kXThreads;
+        p.x_smem = (size_t)p.x_lpb * f3::padded(g.Q) * cs + (size_t)p.x_lpb * 3 * sizeof(int);
+    } else {
+        p.x_lpb = 1;
+        p.x_threads = 256;
+        p.x_smem = 0;
     }
     if (g.N3 > 1) {
         int G = pow2_floor(budget / g.P2);
-        if ((long)G * g.P2 > budget) p.ok = false;
         G = G > 16 ? 16 : G;
-        p.y_G = G;
-        p.y_threads = kFftThreads;
-        p.y_smem = (size_t)padded_len(g.P2) * G * cs;
-        int Gz = pow2_floor(budget / (6L * g.P3));
-        if (6L * Gz * g.P3 > budget) p.ok = false;
-        Gz = Gz > 16 ? 16 : Gz;
-        int KY = pow2_floor(budget / (6L * Gz * g.P3));
-        KY = KY > g.H2 ? pow2_floor(g.H2) : KY;
+        if (G < 1 || g.lgP2 > 11) p.ok = false;
+        p.y_G = G < 1 ? 1 : G;
+        p.y_threads = threads_for((long)p.y_G * g.P2);
+        p.y_smem = (size_t)p.y_G * g.P2 * cs;
+        int Gz = Gmin > 16 ? 16 : Gmin, KY = 0;
+        while (Gz >= 1 && (KY = pow2_floor(budget / (6L * Gz * g.P3))) < 1) Gz /= 2;
+        if (Gz < 1 || KY < 1 || g.lgP3 > 7) p.ok = false;
+        Gz = Gz < 1 ? 1 : Gz;
+        KY = KY < 1 ? 1 : KY;
+        const int kyc = pow2_floor(g.H2);
+        KY = KY > kyc ? kyc : KY;
         p.z_G = Gz;
         p.z_KY = KY;
-        p.z_threads = kFftThreads;
-        p.z_smem = (size_t)padded_len(g.P3) * 6 * KY * Gz * cs;
+        p.z_threads = threads_for(6L * KY * Gz * g.P3);
+        p.z_smem = (size_t)6 * KY * Gz * g.P3 * cs;
     } else {
         int G = pow2_floor(budget / (3L * g.P2));
-        if (3L * G * g.P2 > budget) p.ok = false;
         G = G > 16 ? 16 : G;
-        p.yc_G = G;
-        p.yc_threads = kFftThreads;
-        p.yc_smem = (size_t)padded_len(g.P2) * 3 * G * cs;
+        if (G < 1 || g.lgP2 > 11) p.ok = false;
+        p.yc_G = G < 1 ? 1 : G;
+        p.yc_threads = threads_for(3L * p.yc_G * g.P2);
+        p.yc_smem = (size_t)3 * p.yc_G * g.P2 * cs;
     }
     // the kx grouping divides Xp (a multiple of 16)
     const int Gmax = g.N3 > 1 ? (p.y_G > p.z_G ? p.y_G : p.z_G) : p.yc_G;
@@ -402,24 +508,51 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
     const DemagPlan p = demag_plan<T>(g);
     if (!p.ok) return;
     const int nlines = 3 * g.N2 * g.N3;
-    k_x_fwd<T, CELL><<<div_up(nlines, p.x_lpb), p.x_threads, p.x_smem, st>>>(g, b, in, p.x_lpb);
+    if (g.P1 == 1) {
+        k_x_fwd1<T, CELL><<<div_up(nlines, 256), 256, 0, st>>>(g, b, in);
+    } else {
+        f3::lg_dispatch<1, 10>(g.lgQ, [&](auto c) {
+            constexpr int LG = decltype(c)::value;
+            k_x_fwd<T, CELL, LG><<<div_up(nlines, p.x_lpb), p.x_threads, p.x_smem, st>>>(g, b, in, p.x_lpb);
+        });
+    }
     b.mark("demag_x_fwd");
     if (g.N3 > 1) {
         if (g.P2 > 1) {
-            k_y<T><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G, -1);
+            f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
+                constexpr int LG = decltype(c)::value;
+                k_y<T, LG, -1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G);
+            });
             b.mark("demag_y_fwd");
         }
-        k_z_conv<T><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b, p.z_G, p.z_KY);
+        f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
+            constexpr int LG = decltype(c)::value;
+            k_z_conv<T, LG><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b, p.z_G,
+                                                                                                    p.z_KY);
+        });
         b.mark("demag_z_conv");
         if (g.P2 > 1) {
-            k_y<T><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G, +1);
+            f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
+                constexpr int LG = decltype(c)::value;
+                k_y<T, LG, +1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G);
+            });
             b.mark("demag_y_inv");
         }
     } else {
-        k_y_conv<T><<<g.Xp / p.yc_G, p.yc_threads, p.yc_smem, st>>>(g, b, p.yc_G);
+        f3::lg_dispatch<0, 11>(g.lgP2, [&](auto c) {
+            constexpr int LG = decltype(c)::value;
+            k_y_conv<T, LG><<<g.Xp / p.yc_G, p.yc_threads, p.yc_smem, st>>>(g, b, p.yc_G);
+        });
         b.mark("demag_y_conv");
     }
-    k_x_inv<T, CELL><<<div_up(nlines, p.x_lpb), p.x_threads, p.x_smem, st>>>(g, b, out, p.x_lpb);
+    if (g.P1 == 1) {
+        k_x_inv1<T, CELL><<<div_up(nlines, 256), 256, 0, st>>>(g, b, out);
+    } else {
+        f3::lg_dispatch<1, 10>(g.lgQ, [&](auto c) {
+            constexpr int LG = decltype(c)::value;
+            k_x_inv<T, CELL, LG><<<div_up(nlines, p.x_lpb), p.x_threads, p.x_smem, st>>>(g, b, out, p.x_lpb);
+        });
+    }
     b.mark("demag_x_inv");
 }
 

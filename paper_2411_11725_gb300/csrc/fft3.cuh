@@ -1,0 +1,248 @@
+// Block-level power-of-two FFT engine with the transform length fixed at compile time.
+//
+// A length-2^LG transform runs as Stockham stages: a first stage of radix 2^(LG mod 3) (radix 8 when
+// LG is a multiple of 3), then radix-8 stages.  Each thread keeps 8 complex values in registers per
+// stage (one radix-8 butterfly, or several smaller ones).  Because LG, the radices, the sub-transform
+// lengths and the direction are template constants, every index of a stage reduces to shifts, masks
+// and immediate offsets.  The first stage reads its inputs through a caller functor or from shared
+// memory, and the last stage writes through a functor or to shared memory; only the exchanges between
+// stages go through shared memory.
+//
+// Shared-memory layouts of a block's nl lines:
+//   LF (lines fastest):  element i of line l at buf[i * nl + l]   (consecutive threads take
+//                        consecutive lines, so no padding is needed)
+//   line-major:          element i of line l at buf[l * LSZ + pad16(i)], LSZ = padded_len(2^LG)
+//                        (one pad slot per 16 elements breaks the strided bank pattern of the early
+//                        stages)
+#pragma once
+#include <type_traits>
+
+#include "nm_common.cuh"
+
+namespace nm {
+namespace f3 {
+
+__host__ __device__ constexpr int first_lg(int LG) { return LG % 3 == 0 ? 3 : LG % 3; }
+__host__ __device__ constexpr int n_stages(int LG) { return LG == 0 ? 0 : 1 + (LG - first_lg(LG)) / 3; }
+__host__ __device__ constexpr int stage_lg(int LG, int s) { return s == 0 ? first_lg(LG) : 3; }
+__host__ __device__ constexpr int stage_slg(int LG, int s) { return s == 0 ? 0 : first_lg(LG) + 3 * (s - 1); }
+
+__host__ __device__ constexpr int pad16c(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded(int L) { return L + (L >> 4) + 1; }
+
+// cos and sin of 2 pi k / 16 (k mod 16), folded to constants at each call site
+__host__ __device__ constexpr double c16(int k)
+{
+    switch (k & 15) {
+    case 0: return 1.0;
+    case 1: case 15: return 0.92387953251128675613;
+    case 2: case 14: return 0.70710678118654752440;
+    case 3: case 13: return 0.38268343236508977173;
+    case 4: case 12: return 0.0;
+    case 5: case 11: return -0.38268343236508977173;
+    case 6: case 10: return -0.70710678118654752440;
+    case 7: case 9: return -0.92387953251128675613;
+    default: return -1.0;
+    }
+}
+__host__ __device__ constexpr double s16(int k) { return c16(k - 4); }
+
+template <int R>
+__host__ __device__ constexpr int bitrev(int i)
+{
+    int r = 0;
+    for (int b = 1, rb = R >> 1; b < R; b <<= 1, rb >>= 1)
+        if (i & b) r |= rb;
+    return r;
+}
+
+// x_k <- sum_j x_j e^{DIR 2 pi i jk / R}: radix-2 decimation-in-frequency network, X_k in x[bitrev(k)]
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft(Cx<T> *x)
+{
+#pragma unroll
+    for (int h = R / 2; h >= 1; h >>= 1) {
+#pragma unroll
+        for (int s = 0; s < R; s += 2 * h) {
+#pragma unroll
+            for (int k = 0; k < h; ++k) {
+                const Cx<T> a = x[s + k], b = x[s + k + h];
+                x[s + k] = a + b;
+                const Cx<T> d = a - b;
+                const int q = k * (8 / h);  // W_{2h}^k = W_16^q
+                if (q == 0) x[s + k + h] = d;
+                else if (q == 4) x[s + k + h] = mul_si(d, DIR);
+                else {
+                    const T cq = (T)c16(q), sq = (T)(DIR > 0 ? s16(q) : -s16(q));
+                    x[s + k + h] = cx<T>(d.x * cq - d.y * sq, d.x * sq + d.y * cq);
+                }
+            }
+        }
+    }
+}
+
+// v * conj^(DIR>0)(w): the twiddle table holds e^{-2 pi i k / 2^twlg}
+template <typename T, int DIR>
+__device__ __forceinline__ Cx<T> twmul(Cx<T> v, Cx<T> w)
+{
+    if (DIR < 0) return cx<T>(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+    return cx<T>(v.x * w.x + v.y * w.y, v.y * w.x - v.x * w.y);
+}
+
+// Input / output modes of a stage
+enum { IN_FN = 0, IN_SM = 1 };
+enum { OUT_FN = 0, OUT_SM = 1 };
+
+// One stage S of a length-2^LG transform on nl lines (nb = nl * 2^LG / R butterflies).
+template <typename T, int LG, int S, int DIR, bool LF, int IN, int OUT, bool SYNC_IN, bool SYNC_OUT, typename Src,
+          typename Dst>
+__device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl, const FastDiv &nlf,
+                                      const Cx<T> *__restrict__ tw, int twlg, int nin, int nout, const Src &src,
+                                      const Dst &dst)
+{
+    constexpr int RLG = stage_lg(LG, S), R = 1 << RLG, SLG = stage_slg(LG, S), NS = 1 << SLG;
+    constexpr int L = 1 << LG, LR = L >> RLG, LSZ = padded(L), BPT = 8 / R;
+    const int nb = nl * LR;
+    Cx<T> v[BPT][R];
+    int jv[BPT], lv[BPT];
+#pragma unroll
+    for (int c = 0; c < BPT; ++c) {
+        const int b = threadIdx.x + c * blockDim.x;
+        int j, l;
+        if (LF) {
+            j = (int)nlf.div((unsigned)b);
+            l = b - j * nl;
+        } else {
+            j = b & (LR - 1);
+            l = b >> (LG - RLG);
+        }
+        jv[c] = j;
+        lv[c] = l;
+        if (b < nb) {
+            if (IN == IN_FN) {
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = j + r * LR;
+                    v[c][r] = (S > 0 || i < nin) ? src(l, i) : cx<T>(T(0), T(0));
+                }
+            } else if (LF) {
+                const Cx<T> *p = buf + j * nl + l;
+                const int step = LR * nl;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = j + r * LR;
+                    v[c][r] = (S > 0 || i < nin) ? p[r * step] : cx<T>(T(0), T(0));
+                }
+            } else {
+                const Cx<T> *p = buf + l * LSZ;
+                const int pj = pad16c(j);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int i = j + r * LR;
+                    const int a = (LR % 16 == 0) ? pj + r * (LR + LR / 16) : pad16c(i);
+                    v[c][r] = (S > 0 || i < nin) ? p[a] : cx<T>(T(0), T(0));
+                }
+            }
+        }
+    }
+    if (SYNC_IN) __syncthreads();
+    const int sh = twlg - SLG - RLG;
+#pragma unroll
+    for (int c = 0; c < BPT; ++c) {
+        const int b = threadIdx.x + c * blockDim.x;
+        if (b >= nb) continue;
+        const int j = jv[c], l = lv[c];
+        const int k = j & (NS - 1);
+        if (NS > 1) {
+            const int kk = k << sh;
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[c][r] = twmul<T, DIR>(v[c][r], tw[kk * r]);
+        }
+        dft<T, R, DIR>(v[c]);
+        const int d = ((j >> SLG) << (SLG + RLG)) + k;
+        if (OUT == OUT_FN) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int o = d + r * NS;
+                if (o < nout) dst(l, o, v[c][bitrev<R>(r)]);
+            }
+        } else if (LF) {
+            Cx<T> *p = buf + d * nl + l;
+            const int step = NS * nl;
+#pragma unroll
+            for (int r = 0; r < R; ++r) p[r * step] = v[c][bitrev<R>(r)];
+        } else {
+            Cx<T> *p = buf + l * LSZ;
+            const int pd = pad16c(d);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int a = (NS % 16 == 0) ? pd + r * (NS + NS / 16) : pad16c(d + r * NS);
+                p[a] = v[c][bitrev<R>(r)];
+            }
+        }
+    }
+    if (SYNC_OUT) __syncthreads();
+}
+
+template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, typename Src, typename Dst>
+__device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw,
+                                           int twlg, int nin, int nout, const Src &src, const Dst &dst)
+{
+    constexpr int NSG = n_stages(LG);
+    if constexpr (S < NSG) {
+        constexpr bool first = S == 0, last = S + 1 == NSG;
+        constexpr int IN = (first && !SRC_SM) ? IN_FN : IN_SM;
+        constexpr int OUT = (last && !DST_SM) ? OUT_FN : OUT_SM;
+        constexpr bool SYNC_IN = IN == IN_SM && OUT == OUT_SM;  // in place: all reads before any write
+        constexpr bool SYNC_OUT = OUT == OUT_SM;
+        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT>(buf, nl, nlf, tw, twlg, first ? nin : (1 << LG),
+                                                          last ? nout : (1 << LG), src, dst);
+        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+    }
+}
+
+// Transform nl lines of length 2^LG (LG >= 1): inputs i >= nin are zero, outputs o >= nout dropped.
+// SRC_SM: the first stage reads the shared layout (the caller synchronised after filling it);
+// otherwise src(l, i) is called for i < nin.  DST_SM: the last stage writes the shared layout
+// (followed by a barrier); otherwise dst(l, o, v) is called for o < nout.
+// Needs nl * 2^LG <= 8 * blockDim.x.
+template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, typename Src, typename Dst>
+__device__ __forceinline__ void fft(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw, int twlg,
+                                    int nin, int nout, const Src &src, const Dst &dst)
+{
+    static_assert(LG >= 1, "length-1 transforms are copies");
+    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+}
+
+// placeholder functor for a stage side that is shared memory
+template <typename T>
+struct NoFn {
+    __device__ Cx<T> operator()(int, int) const { return cx<T>(T(0), T(0)); }
+    __device__ void operator()(int, int, Cx<T>) const {}
+};
+
+// Compile-time dispatch of a runtime log2 length in [LO, HI]
+template <int LO, int HI, typename F>
+inline bool lg_dispatch(int lg, F &&f)
+{
+    if constexpr (LO <= HI) {
+        if (lg == LO) {
+            f(std::integral_constant<int, LO>{});
+            return true;
+        }
+        return lg_dispatch<LO + 1, HI>(lg, f);
+    } else {
+        return false;
+    }
+}
+template <int LO, int HI, typename F>
+inline void lg_for_each(F &&f)
+{
+    if constexpr (LO <= HI) {
+        f(std::integral_constant<int, LO>{});
+        lg_for_each<LO + 1, HI>(f);
+    }
+}
+
+}  // namespace f3
+}  // namespace nm
