@@ -19,6 +19,58 @@ __device__ __forceinline__ double time_factor(double f, double ph, double t)
     return f == 0.0 ? 1.0 : sin(2.0 * 3.14159265358979323846 * f * t + ph);
 }
 
+// The node kernel walks a TX x TY tile of nodes along z.  Three node planes of y (z-1, z, z+1, with a
+// one-node halo in x and y) and two cell planes of Ms_c H_c (z-1, z, with the cells around the tile)
+// rotate through shared memory, so every value is read from global memory about once.  Nodes and cells
+// outside the mesh are stored as zeros (their weights are zero too).
+constexpr int kTX = 32, kTY = 8;
+constexpr int kSX = kTX + 2, kSY = kTY + 2;    // node plane with halo
+constexpr int kCX = kTX + 1, kCY = kTY + 1;    // cell plane around the tile
+
+template <typename T>
+struct NodeSmem {
+    T y[3][3][kSY][kSX];   // [slot = z mod 3][component][row][column]
+    T c[2][3][kCY][kCX];   // [slot = c3 mod 2][component][row][column], Ms_c H_c
+    T hf[4];
+};
+
+template <typename T>
+__device__ __forceinline__ void load_node_plane(const LocalParams<T> &p, const T *__restrict__ y, NodeSmem<T> &sm,
+                                                int z, int x0, int y0)
+{
+    const Geom &g = p.g;
+    T(*dst)[kSY][kSX] = sm.y[(z + 3) % 3];
+    const bool zin = z >= 0 && z < g.nn3;
+    const int ns = (int)g.ns;
+    for (int t = threadIdx.x; t < kSX * kSY; t += blockDim.x) {
+        const int r = t / kSX, cc = t - r * kSX;
+        const int nx = x0 - 1 + cc, ny = y0 - 1 + r;
+        const bool in = zin && nx >= 0 && nx < g.nn1 && ny >= 0 && ny < g.nn2;
+        const int n = in ? (z * g.nn2 + ny) * g.nn1 + nx : 0;
+        dst[0][r][cc] = in ? y[n] : T(0);
+        dst[1][r][cc] = in ? y[ns + n] : T(0);
+        dst[2][r][cc] = in ? y[2 * ns + n] : T(0);
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_cell_plane(const LocalParams<T> &p, NodeSmem<T> &sm, int c3, int x0, int y0)
+{
+    const Geom &g = p.g;
+    T(*dst)[kCY][kCX] = sm.c[(c3 + 2) % 2];
+    const bool zin = c3 >= 0 && c3 < g.N3 && p.MsH != nullptr && (p.terms & NM_DEMAG);
+    const int cs = (int)g.cs;
+    for (int t = threadIdx.x; t < kCX * kCY; t += blockDim.x) {
+        const int r = t / kCX, cc = t - r * kCX;
+        const int c1 = x0 - 1 + cc, c2 = y0 - 1 + r;
+        const bool in = zin && c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2;
+        const int c = in ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
+        dst[0][r][cc] = in ? p.MsH[c] : T(0);
+        dst[1][r][cc] = in ? p.MsH[cs + c] : T(0);
+        dst[2][r][cc] = in ? p.MsH[2 * cs + c] : T(0);
+    }
+}
+
 template <typename T>
 struct NodeField {
     T hx, hy, hz;
@@ -26,109 +78,95 @@ struct NodeField {
     bool magnetic;
 };
 
-// Applied-field factors at time t, computed once per block: (h_uniform * s_u(t), s_c(t)).
+// Effective field at node (n1, n2, n3) = (x0 + tx, y0 + ty, z) from the shared planes.
 template <typename T>
-__device__ __forceinline__ void block_field_factors(const LocalParams<T> &p, double t, T out[4])
-{
-    __shared__ T sh[4];
-    if (threadIdx.x == 0) {
-        const double su = time_factor<T>(p.hu_freq, p.hu_phase, t);
-        sh[0] = (T)(p.hu0 * su);
-        sh[1] = (T)(p.hu1 * su);
-        sh[2] = (T)(p.hu2 * su);
-        sh[3] = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
-    }
-    __syncthreads();
-    out[0] = sh[0]; out[1] = sh[1]; out[2] = sh[2]; out[3] = sh[3];
-}
-
-template <typename T>
-__device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const T *__restrict__ y, long n,
-                                                   const T hf[4])
+__device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const NodeSmem<T> &sm, int n1, int n2,
+                                                   int n3, int n, int tx, int ty)
 {
     const Geom &g = p.g;
-    const int n1 = (int)(n % g.nn1);
-    const long r = n / g.nn1;
-    const int n2 = (int)(r % g.nn2);
-    const int n3 = (int)(r / g.nn2);
     T a[8], ku[8];
-    long cidx[8];
-    bool cval[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-        int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
-        bool valid = c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3;
-        long c = valid ? ((long)c3 * g.N2 + c2) * g.N1 + c1 : 0;
-        T Ms = valid ? (p.Ms ? p.Ms[c] : p.Ms0) : T(0);
-        bool mag = valid && Ms > T(0);
+        const int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+        const bool valid = c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3;
+        const int c = valid ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
+        const T Ms = valid ? (p.Ms ? p.Ms[c] : p.Ms0) : T(0);
+        const bool mag = valid && Ms > T(0);
         a[i] = (mag && (p.terms & NM_EXCH)) ? (p.A ? p.A[c] : p.A0) : T(0);
         ku[i] = (mag && (p.terms & NM_ANIS)) ? (p.Ku ? p.Ku[c] : p.Ku0) : T(0);
-        cidx[i] = c;
-        cval[i] = valid;
     }
-    const long ns = g.ns;
+    const int sz0 = (n3 + 3) % 3, szm = (n3 + 2) % 3, szp = (n3 + 1) % 3;
+    const int cx0 = tx + 1, cy0 = ty + 1;
     NodeField<T> f;
-    f.mx = y[n];
-    f.my = y[ns + n];
-    f.mz = y[2 * ns + n];
+    f.mx = sm.y[sz0][0][cy0][cx0];
+    f.my = sm.y[sz0][1][cy0][cx0];
+    f.mz = sm.y[sz0][2][cy0][cx0];
     const T im = p.inv_mass[n];
     f.magnetic = im > T(0);
     T ex = 0, ey = 0, ez = 0, pe = 0;
-    const long sy = g.nn1, sz = (long)g.nn1 * g.nn2;
 #pragma unroll
-    for (int o1 = -1; o1 <= 1; ++o1)
+    for (int o3 = -1; o3 <= 1; ++o3) {
+        const int slot = o3 < 0 ? szm : (o3 > 0 ? szp : sz0);
 #pragma unroll
         for (int o2 = -1; o2 <= 1; ++o2)
 #pragma unroll
-            for (int o3 = -1; o3 <= 1; ++o3) {
+            for (int o1 = -1; o1 <= 1; ++o1) {
                 T S = 0, K = 0;
 #pragma unroll
                 for (int i = 0; i < 8; ++i) {
-                    int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
-                    bool comp = (o1 == -1 ? i1 == 1 : (o1 == 1 ? i1 == 0 : true)) &&
-                                (o2 == -1 ? i2 == 1 : (o2 == 1 ? i2 == 0 : true)) &&
-                                (o3 == -1 ? i3 == 1 : (o3 == 1 ? i3 == 0 : true));
-                    if (comp) { S += a[i]; K += ku[i]; }
+                    const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
+                    const bool comp = (o1 == -1 ? i1 == 1 : (o1 == 1 ? i1 == 0 : true)) &&
+                                      (o2 == -1 ? i2 == 1 : (o2 == 1 ? i2 == 0 : true)) &&
+                                      (o3 == -1 ? i3 == 1 : (o3 == 1 ? i3 == 0 : true));
+                    if (comp) {
+                        S += a[i];
+                        K += ku[i];
+                    }
                 }
                 const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
                 const bool self = (o1 == 0 && o2 == 0 && o3 == 0);
-                if ((!self && S != T(0)) || K != T(0)) {
-                    long nb = n + o1 + o2 * sy + o3 * sz;
-                    T qx = self ? f.mx : y[nb], qy = self ? f.my : y[ns + nb], qz = self ? f.mz : y[2 * ns + nb];
-                    if (!self) {
-                        T w = p.Wex[d] * S;
-                        ex += w * (qx - f.mx);
-                        ey += w * (qy - f.my);
-                        ez += w * (qz - f.mz);
-                    }
-                    pe += p.Wm[d] * K * (p.e0 * qx + p.e1 * qy + p.e2 * qz);
+                const T qx = self ? f.mx : sm.y[slot][0][cy0 + o2][cx0 + o1];
+                const T qy = self ? f.my : sm.y[slot][1][cy0 + o2][cx0 + o1];
+                const T qz = self ? f.mz : sm.y[slot][2][cy0 + o2][cx0 + o1];
+                if (!self) {
+                    const T w = p.Wex[d] * S;
+                    ex += w * (qx - f.mx);
+                    ey += w * (qy - f.my);
+                    ez += w * (qz - f.mz);
                 }
+                pe += p.Wm[d] * K * (p.e0 * qx + p.e1 * qy + p.e2 * qz);
             }
+    }
     // -dE / mass: exchange and anisotropy
     T hx = -ex + T(2) * p.e0 * pe;
     T hy = -ey + T(2) * p.e1 * pe;
     T hz = -ez + T(2) * p.e2 * pe;
-    // cell -> node: demag (Ms_c H_c) and cell applied field (Ms_c h_c), weight mu0 V/8
+    // cell -> node: demag (Ms_c H_c, from the shared cell planes) and cell applied field (Ms_c h_c)
     T cx_ = 0, cy_ = 0, cz_ = 0;
     if (p.MsH && (p.terms & NM_DEMAG)) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (cval[i]) {
-                cx_ += p.MsH[cidx[i]];
-                cy_ += p.MsH[g.cs + cidx[i]];
-                cz_ += p.MsH[2 * g.cs + cidx[i]];
-            }
+        for (int i = 0; i < 8; ++i) {
+            const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
+            const int cs_ = (n3 - i3 + 2) % 2;
+            cx_ += sm.c[cs_][0][cy0 - i2][cx0 - i1];
+            cy_ += sm.c[cs_][1][cy0 - i2][cx0 - i1];
+            cz_ += sm.c[cs_][2][cy0 - i2][cx0 - i1];
+        }
     }
     if (p.Msh && (p.terms & NM_ZEE)) {
-        const T sc = hf[3];
+        const T sc = sm.hf[3];
+        const long cs = g.cs;
         T ax = 0, ay = 0, az = 0;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (cval[i]) {
-                ax += p.Msh[cidx[i]];
-                ay += p.Msh[g.cs + cidx[i]];
-                az += p.Msh[2 * g.cs + cidx[i]];
+        for (int i = 0; i < 8; ++i) {
+            const int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+            if (c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3) {
+                const int c = (c3 * g.N2 + c2) * g.N1 + c1;
+                ax += p.Msh[c];
+                ay += p.Msh[cs + c];
+                az += p.Msh[2 * cs + c];
             }
+        }
         cx_ += sc * ax;
         cy_ += sc * ay;
         cz_ += sc * az;
@@ -144,90 +182,124 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
     hy = im * (hy + p.mu0V8 * cy_);
     hz = im * (hz + p.mu0V8 * cz_);
     if (f.magnetic && (p.terms & NM_ZEE)) {
-        hx += hf[0];
-        hy += hf[1];
-        hz += hf[2];
+        hx += sm.hf[0];
+        hy += sm.hf[1];
+        hz += sm.hf[2];
     }
     f.hx = hx; f.hy = hy; f.hz = hz;
     return f;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) k_heff(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ h, double t)
+// STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
+// input.  Block (bx, by, bz) covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [bz*zc, bz*zc+zc).
+template <typename T, bool STAGE>
+__global__ void __launch_bounds__(kTX *kTY) k_node(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ out,
+                                                   T *__restrict__ y_next, StageArgs sa, double t_heff, int zc)
 {
-    T hf[4];
-    block_field_factors(p, t, hf);
-    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (n >= p.g.n_nodes) return;
-    NodeField<T> f = node_field(p, y, n, hf);
-    const long ns = p.g.ns;
-    h[n] = f.hx;
-    h[ns + n] = f.hy;
-    h[2 * ns + n] = f.hz;
+    if (STAGE && sa.ctl && sa.ctl->done) return;
+    __shared__ NodeSmem<T> sm;
+    const Geom &g = p.g;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int z0 = blockIdx.z * zc, z1 = min(g.nn3, z0 + zc);
+    const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
+    const int n1 = x0 + tx, n2 = y0 + ty;
+    const bool active = n1 < g.nn1 && n2 < g.nn2;
+    if (threadIdx.x == 0) {
+        const double t = STAGE ? (sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed) : t_heff;
+        const double su = time_factor<T>(p.hu_freq, p.hu_phase, t);
+        sm.hf[0] = (T)(p.hu0 * su);
+        sm.hf[1] = (T)(p.hu1 * su);
+        sm.hf[2] = (T)(p.hu2 * su);
+        sm.hf[3] = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
+    }
+    load_node_plane(p, y, sm, z0 - 1, x0, y0);
+    load_node_plane(p, y, sm, z0, x0, y0);
+    load_cell_plane(p, sm, z0 - 1, x0, y0);
+    const int ns = (int)g.ns;
+    double dt = 0.0;
+    if (STAGE) dt = sa.ctl ? sa.ctl->dt : 0.0;
+    for (int z = z0; z < z1; ++z) {
+        load_node_plane(p, y, sm, z + 1, x0, y0);
+        load_cell_plane(p, sm, z, x0, y0);
+        __syncthreads();
+        if (active) {
+            const int n = (z * g.nn2 + n2) * g.nn1 + n1;
+            const NodeField<T> f = node_field(p, sm, n1, n2, z, n, tx, ty);
+            if (!STAGE) {
+                out[n] = f.hx;
+                out[ns + n] = f.hy;
+                out[2 * ns + n] = f.hz;
+            } else {
+                T kx = 0, ky = 0, kz = 0;
+                if (f.magnetic) {
+                    // k = -gamma'(m x H + alpha m x (m x H))
+                    const T ax = f.my * f.hz - f.mz * f.hy;
+                    const T ay = f.mz * f.hx - f.mx * f.hz;
+                    const T az = f.mx * f.hy - f.my * f.hx;
+                    const T bx = f.my * az - f.mz * ay;
+                    const T by = f.mz * ax - f.mx * az;
+                    const T bz = f.mx * ay - f.my * ax;
+                    const T gm = (T)p.gam, al = (T)p.alpha;
+                    kx = -gm * (ax + al * bx);
+                    ky = -gm * (ay + al * by);
+                    kz = -gm * (az + al * bz);
+                }
+                out[n] = kx;
+                out[ns + n] = ky;
+                out[2 * ns + n] = kz;
+                if (y_next) {
+                    // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working
+                    // precision, the addition to the FP64 magnetisation in FP64
+                    T ax = 0, ay = 0, az = 0;
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) {
+                        if (j + 1 >= sa.s) break;
+                        const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
+                        if (aj == T(0)) continue;
+                        const T *kj = (const T *)sa.k[j];
+                        ax += aj * kj[n];
+                        ay += aj * kj[ns + n];
+                        az += aj * kj[2 * ns + n];
+                    }
+                    const T as = sizeof(T) == 4 ? (T)sa.af[sa.s - 1] : (T)sa.a[sa.s - 1];
+                    ax += as * kx;
+                    ay += as * ky;
+                    az += as * kz;
+                    y_next[n] = (T)(sa.m[n] + dt * (double)ax);
+                    y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)ay);
+                    y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)az);
+                }
+            }
+        }
+        __syncthreads();  // the next iteration overwrites the slots of planes z - 1 and c3 = z - 1
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_llg_stage(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ k_out,
-                                                   T *__restrict__ y_next, StageArgs sa)
+static dim3 node_grid(const Geom &g, int *zc)
 {
-    if (sa.ctl && sa.ctl->done) return;
-    const double t = sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed;
-    T hf[4];
-    block_field_factors(p, t, hf);
-    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (n >= p.g.n_nodes) return;
-    NodeField<T> f = node_field(p, y, n, hf);
-    const long ns = p.g.ns;
-    T kx = 0, ky = 0, kz = 0;
-    if (f.magnetic) {
-        // k = -gamma'(m x H + alpha m x (m x H))
-        T ax = f.my * f.hz - f.mz * f.hy;
-        T ay = f.mz * f.hx - f.mx * f.hz;
-        T az = f.mx * f.hy - f.my * f.hx;
-        T bx = f.my * az - f.mz * ay;
-        T by = f.mz * ax - f.mx * az;
-        T bz = f.mx * ay - f.my * ax;
-        T gm = (T)p.gam, al = (T)p.alpha;
-        kx = -gm * (ax + al * bx);
-        ky = -gm * (ay + al * by);
-        kz = -gm * (az + al * bz);
-    }
-    k_out[n] = kx;
-    k_out[ns + n] = ky;
-    k_out[2 * ns + n] = kz;
-    if (y_next) {
-        // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working precision,
-        // the addition to the FP64 magnetisation in FP64
-        const double dt = sa.ctl ? sa.ctl->dt : 0.0;
-        T ax = 0, ay = 0, az = 0;
-        for (int j = 0; j + 1 < sa.s; ++j) {
-            const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
-            if (aj == T(0)) continue;
-            const T *kj = (const T *)sa.k[j];
-            ax += aj * kj[n];
-            ay += aj * kj[ns + n];
-            az += aj * kj[2 * ns + n];
-        }
-        const T as = sizeof(T) == 4 ? (T)sa.af[sa.s - 1] : (T)sa.a[sa.s - 1];
-        ax += as * kx;
-        ay += as * ky;
-        az += as * kz;
-        y_next[n] = (T)(sa.m[n] + dt * (double)ax);
-        y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)ay);
-        y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)az);
-    }
+    const int bx = div_up(g.nn1, kTX), by = div_up(g.nn2, kTY);
+    const long bxy = (long)bx * by;
+    int chunks = (int)((4L * 152 + bxy - 1) / bxy);
+    chunks = chunks < 1 ? 1 : (chunks > g.nn3 ? g.nn3 : chunks);
+    *zc = div_up(g.nn3, chunks);
+    return dim3(bx, by, div_up(g.nn3, *zc));
 }
 
 template <typename T>
 void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaStream_t st)
 {
-    k_heff<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, h_out, t);
+    int zc;
+    const dim3 grid = node_grid<T>(p.g, &zc);
+    k_node<T, false><<<grid, kTX * kTY, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
 }
 
 template <typename T>
 void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, const StageArgs &sa, cudaStream_t st)
 {
-    k_llg_stage<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, k_out, y_next, sa);
+    int zc;
+    const dim3 grid = node_grid<T>(p.g, &zc);
+    k_node<T, true><<<grid, kTX * kTY, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
 }
 
 // ---------------------------------------------------------------------------------------------
