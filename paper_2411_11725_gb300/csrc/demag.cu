@@ -15,8 +15,15 @@
 namespace nm {
 
 constexpr int kXThreads = 256;
+// y and z passes: 512-thread blocks, two per SM in FP32 (one block's loads and barriers overlap the
+// other's arithmetic); the longest y lines (2^11) take 1024 threads so that a block still spans 4 columns.
+template <typename T, int LG = 0>
+constexpr int kMaxThreads = (sizeof(T) == 4 && LG >= 11) ? 1024 : 512;
+template <typename T, int LG = 0>
+constexpr int kMinBlocks = (sizeof(T) == 4 && LG < 11) ? 2 : 1;
+// the single-layer pass keeps up to 1024 threads (FP32) so that long y lines still fit one block
 template <typename T>
-constexpr int kMaxThreads = sizeof(T) == 4 ? 1024 : 512;
+constexpr int kMaxThreadsYC = sizeof(T) == 4 ? 1024 : 512;
 
 // Asynchronous global -> shared copies (cp.async): many in flight per thread without registers.
 __device__ __forceinline__ void cpa16(void *sm, const void *gm)
@@ -230,7 +237,7 @@ __global__ void k_x_inv1(Geom g, DemagBufs<T> b, T *__restrict__ out)
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
 // Shared layout: row y at buf + y * G (lines = columns, fastest).
 template <typename T, int LG, int DIR>
-__global__ void __launch_bounds__(kMaxThreads<T>, 1) k_y(Geom g, DemagBufs<T> b, int G)
+__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geom g, DemagBufs<T> b, int G)
 {
     if (b.ctl && b.ctl->done) return;
     constexpr int P2 = 1 << LG;
@@ -287,7 +294,7 @@ __device__ __forceinline__ void tensor_mul(const Ten6<T> &t, T s2, Cx<T> *px, Cx
 // Rows r < KY are ky = a2_0 + r, rows KY + r are ky = P2 - (a2_0 + r) (present when 0 < a2 < P2/2).
 // Lines l = (c * 2KY + r) * G + g; element kz of line l at buf[kz * nl + l].
 template <typename T, int LG>
-__global__ void __launch_bounds__(kMaxThreads<T>, 1) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
+__global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
 {
     if (b.ctl && b.ctl->done) return;
     constexpr int P3 = 1 << LG;
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(kMaxThreads<T>, 1) k_z_conv(Geom g, DemagBufs<
 // read once and applied to ky = a2 and P2 - a2), inverse y.  Lines l = c * G + g; element y of line l
 // at buf[y * nl + l].  LG = 0 (N2 == 1): the product alone.
 template <typename T, int LG>
-__global__ void __launch_bounds__(kMaxThreads<T>, 1) k_y_conv(Geom g, DemagBufs<T> b, int G)
+__global__ void __launch_bounds__(kMaxThreadsYC<T>, 1) k_y_conv(Geom g, DemagBufs<T> b, int G)
 {
     if (b.ctl && b.ctl->done) return;
     constexpr int P2 = 1 << LG;
@@ -469,7 +476,8 @@ DemagPlan demag_plan(const Geom &g)
         p.x_smem = 0;
     }
     if (g.N3 > 1) {
-        int G = pow2_floor(budget / g.P2);
+        const long ybudget = 8L * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 1024 : 512);
+        int G = pow2_floor(ybudget / g.P2);
         G = G > 16 ? 16 : G;
         if (G < 1 || g.lgP2 > 11) p.ok = false;
         p.y_G = G < 1 ? 1 : G;
@@ -487,7 +495,7 @@ DemagPlan demag_plan(const Geom &g)
         p.z_threads = threads_for(6L * KY * Gz * g.P3);
         p.z_smem = (size_t)6 * KY * Gz * g.P3 * cs;
     } else {
-        int G = pow2_floor(budget / (3L * g.P2));
+        int G = pow2_floor(8L * kMaxThreadsYC<T> / (3L * g.P2));
         G = G > 16 ? 16 : G;
         if (G < 1 || g.lgP2 > 11) p.ok = false;
         p.yc_G = G < 1 ? 1 : G;

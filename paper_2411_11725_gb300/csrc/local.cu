@@ -19,55 +19,84 @@ __device__ __forceinline__ double time_factor(double f, double ph, double t)
     return f == 0.0 ? 1.0 : sin(2.0 * 3.14159265358979323846 * f * t + ph);
 }
 
-// The node kernel walks a TX x TY tile of nodes along z.  Three node planes of y (z-1, z, z+1, with a
-// one-node halo in x and y) and two cell planes of Ms_c H_c (z-1, z, with the cells around the tile)
-// rotate through shared memory, so every value is read from global memory about once.  Nodes and cells
-// outside the mesh are stored as zeros (their weights are zero too).
-constexpr int kTX = 32, kTY = 8;
-constexpr int kSX = kTX + 2, kSY = kTY + 2;    // node plane with halo
-constexpr int kCX = kTX + 1, kCY = kTY + 1;    // cell plane around the tile
+// The node kernel walks a TX x TY tile of nodes along z.  Node planes of y (with a one-node halo in x
+// and y) and cell planes of Ms_c H_c (the cells around the tile) rotate through shared memory: planes
+// z-1, z, z+1 are read while plane z+2 (and cell plane z+1) are already being copied in with cp.async,
+// so every value is read from global memory about once and the copies overlap the arithmetic.  Nodes
+// and cells outside the mesh are filled with zeros (their weights are zero too).
+constexpr int kTX = 32;
+template <typename T>
+constexpr int kTY = sizeof(T) == 4 ? 8 : 4;  // FP64 tiles are half as high (shared-memory limit)
+constexpr int kNodeSlots = 4, kCellSlots = 3;
+
+// a nodal or cell 3-vector in shared memory: padded to one 16-byte access in FP32, packed in FP64
+template <typename T>
+struct V4 {
+    T x, y, z;
+};
+template <>
+struct alignas(16) V4<float> {
+    float x, y, z, w;
+};
 
 template <typename T>
 struct NodeSmem {
-    T y[3][3][kSY][kSX];   // [slot = z mod 3][component][row][column]
-    T c[2][3][kCY][kCX];   // [slot = c3 mod 2][component][row][column], Ms_c H_c
+    static constexpr int SX = kTX + 2, SY = kTY<T> + 2;  // node plane with halo
+    static constexpr int CX = kTX + 1, CY = kTY<T> + 1;  // cell plane around the tile
+    V4<T> y[kNodeSlots][SY][SX];   // node plane z in slot (z + 4) % 4
+    V4<T> c[kCellSlots][CY][CX];   // cell plane c3 in slot (c3 + 3) % 3, Ms_c H_c
     T hf[4];
 };
+
+// asynchronous copy of one value, or zero fill when !in
+template <typename T>
+__device__ __forceinline__ void cp_val(T *dst, const T *src, bool in)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const int n = in ? (int)sizeof(T) : 0;
+    if (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
 
 template <typename T>
 __device__ __forceinline__ void load_node_plane(const LocalParams<T> &p, const T *__restrict__ y, NodeSmem<T> &sm,
                                                 int z, int x0, int y0)
 {
+    using S = NodeSmem<T>;
     const Geom &g = p.g;
-    T(*dst)[kSY][kSX] = sm.y[(z + 3) % 3];
+    V4<T>(*dst)[S::SX] = sm.y[(z + kNodeSlots) % kNodeSlots];
     const bool zin = z >= 0 && z < g.nn3;
     const int ns = (int)g.ns;
-    for (int t = threadIdx.x; t < kSX * kSY; t += blockDim.x) {
-        const int r = t / kSX, cc = t - r * kSX;
+    for (int t = threadIdx.x; t < S::SX * S::SY; t += blockDim.x) {
+        const int r = t / S::SX, cc = t - r * S::SX;
         const int nx = x0 - 1 + cc, ny = y0 - 1 + r;
         const bool in = zin && nx >= 0 && nx < g.nn1 && ny >= 0 && ny < g.nn2;
         const int n = in ? (z * g.nn2 + ny) * g.nn1 + nx : 0;
-        dst[0][r][cc] = in ? y[n] : T(0);
-        dst[1][r][cc] = in ? y[ns + n] : T(0);
-        dst[2][r][cc] = in ? y[2 * ns + n] : T(0);
+        cp_val(&dst[r][cc].x, y + n, in);
+        cp_val(&dst[r][cc].y, y + ns + n, in);
+        cp_val(&dst[r][cc].z, y + 2 * ns + n, in);
     }
 }
 
 template <typename T>
 __device__ __forceinline__ void load_cell_plane(const LocalParams<T> &p, NodeSmem<T> &sm, int c3, int x0, int y0)
 {
+    using S = NodeSmem<T>;
     const Geom &g = p.g;
-    T(*dst)[kCY][kCX] = sm.c[(c3 + 2) % 2];
-    const bool zin = c3 >= 0 && c3 < g.N3 && p.MsH != nullptr && (p.terms & NM_DEMAG);
+    if (!p.MsH || !(p.terms & NM_DEMAG)) return;  // the cell planes are not read
+    V4<T>(*dst)[S::CX] = sm.c[(c3 + kCellSlots) % kCellSlots];
+    const bool zin = c3 >= 0 && c3 < g.N3;
     const int cs = (int)g.cs;
-    for (int t = threadIdx.x; t < kCX * kCY; t += blockDim.x) {
-        const int r = t / kCX, cc = t - r * kCX;
+    for (int t = threadIdx.x; t < S::CX * S::CY; t += blockDim.x) {
+        const int r = t / S::CX, cc = t - r * S::CX;
         const int c1 = x0 - 1 + cc, c2 = y0 - 1 + r;
         const bool in = zin && c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2;
         const int c = in ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
-        dst[0][r][cc] = in ? p.MsH[c] : T(0);
-        dst[1][r][cc] = in ? p.MsH[cs + c] : T(0);
-        dst[2][r][cc] = in ? p.MsH[2 * cs + c] : T(0);
+        cp_val(&dst[r][cc].x, p.MsH + c, in);
+        cp_val(&dst[r][cc].y, p.MsH + cs + c, in);
+        cp_val(&dst[r][cc].z, p.MsH + 2 * cs + c, in);
     }
 }
 
@@ -78,64 +107,96 @@ struct NodeField {
     bool magnetic;
 };
 
-// Effective field at node (n1, n2, n3) = (x0 + tx, y0 + ty, z) from the shared planes.
-template <typename T>
+// Effective field at node (n1, n2, n3) = (x0 + tx, y0 + ty, z) from the shared planes.  INTERIOR:
+// every cell around the node exists and the material is uniform, so the 27 assembled weights are
+// constants.
+template <typename T, bool INTERIOR>
 __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const NodeSmem<T> &sm, int n1, int n2,
                                                    int n3, int n, int tx, int ty)
 {
     const Geom &g = p.g;
-    T a[8], ku[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
-        const bool valid = c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3;
-        const int c = valid ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
-        const T Ms = valid ? (p.Ms ? p.Ms[c] : p.Ms0) : T(0);
-        const bool mag = valid && Ms > T(0);
-        a[i] = (mag && (p.terms & NM_EXCH)) ? (p.A ? p.A[c] : p.A0) : T(0);
-        ku[i] = (mag && (p.terms & NM_ANIS)) ? (p.Ku ? p.Ku[c] : p.Ku0) : T(0);
-    }
-    const int sz0 = (n3 + 3) % 3, szm = (n3 + 2) % 3, szp = (n3 + 1) % 3;
+    const int sz0 = (n3 + kNodeSlots) % kNodeSlots, szm = (n3 + kNodeSlots - 1) % kNodeSlots,
+              szp = (n3 + 1) % kNodeSlots;
     const int cx0 = tx + 1, cy0 = ty + 1;
     NodeField<T> f;
-    f.mx = sm.y[sz0][0][cy0][cx0];
-    f.my = sm.y[sz0][1][cy0][cx0];
-    f.mz = sm.y[sz0][2][cy0][cx0];
+    {
+        const V4<T> m = sm.y[sz0][cy0][cx0];
+        f.mx = m.x;
+        f.my = m.y;
+        f.mz = m.z;
+    }
     const T im = p.inv_mass[n];
     f.magnetic = im > T(0);
     T ex = 0, ey = 0, ez = 0, pe = 0;
+    if (INTERIOR) {
+        // sum_o w_o (m_{n+o} - m_n) = sum_{o != 0} w_o m_{n+o} - (sum w) m_n;  anisotropy: sum_o c_o m_{n+o}
+        T sx = 0, sy = 0, sz = 0, ax = 0, ay = 0, az = 0;
 #pragma unroll
-    for (int o3 = -1; o3 <= 1; ++o3) {
-        const int slot = o3 < 0 ? szm : (o3 > 0 ? szp : sz0);
+        for (int o3 = -1; o3 <= 1; ++o3) {
+            const int slot = o3 < 0 ? szm : (o3 > 0 ? szp : sz0);
 #pragma unroll
-        for (int o2 = -1; o2 <= 1; ++o2)
+            for (int o2 = -1; o2 <= 1; ++o2)
 #pragma unroll
-            for (int o1 = -1; o1 <= 1; ++o1) {
-                T S = 0, K = 0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
-                    const bool comp = (o1 == -1 ? i1 == 1 : (o1 == 1 ? i1 == 0 : true)) &&
-                                      (o2 == -1 ? i2 == 1 : (o2 == 1 ? i2 == 0 : true)) &&
-                                      (o3 == -1 ? i3 == 1 : (o3 == 1 ? i3 == 0 : true));
-                    if (comp) {
-                        S += a[i];
-                        K += ku[i];
+                for (int o1 = -1; o1 <= 1; ++o1) {
+                    const int k = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
+                    const V4<T> q = sm.y[slot][cy0 + o2][cx0 + o1];
+                    if (k != 13) {
+                        sx += p.wex27[k] * q.x;
+                        sy += p.wex27[k] * q.y;
+                        sz += p.wex27[k] * q.z;
                     }
+                    ax += p.wan27[k] * q.x;
+                    ay += p.wan27[k] * q.y;
+                    az += p.wan27[k] * q.z;
                 }
-                const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
-                const bool self = (o1 == 0 && o2 == 0 && o3 == 0);
-                const T qx = self ? f.mx : sm.y[slot][0][cy0 + o2][cx0 + o1];
-                const T qy = self ? f.my : sm.y[slot][1][cy0 + o2][cx0 + o1];
-                const T qz = self ? f.mz : sm.y[slot][2][cy0 + o2][cx0 + o1];
-                if (!self) {
-                    const T w = p.Wex[d] * S;
-                    ex += w * (qx - f.mx);
-                    ey += w * (qy - f.my);
-                    ez += w * (qz - f.mz);
+        }
+        ex = sx - p.wex_sum * f.mx;
+        ey = sy - p.wex_sum * f.my;
+        ez = sz - p.wex_sum * f.mz;
+        pe = p.e0 * ax + p.e1 * ay + p.e2 * az;
+    } else {
+        T a[8], ku[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+            const bool valid = c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3;
+            const int c = valid ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
+            const T Ms = valid ? (p.Ms ? p.Ms[c] : p.Ms0) : T(0);
+            const bool mag = valid && Ms > T(0);
+            a[i] = (mag && (p.terms & NM_EXCH)) ? (p.A ? p.A[c] : p.A0) : T(0);
+            ku[i] = (mag && (p.terms & NM_ANIS)) ? (p.Ku ? p.Ku[c] : p.Ku0) : T(0);
+        }
+#pragma unroll
+        for (int o3 = -1; o3 <= 1; ++o3) {
+            const int slot = o3 < 0 ? szm : (o3 > 0 ? szp : sz0);
+#pragma unroll
+            for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+                for (int o1 = -1; o1 <= 1; ++o1) {
+                    T S = 0, K = 0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
+                        const bool comp = (o1 == -1 ? i1 == 1 : (o1 == 1 ? i1 == 0 : true)) &&
+                                          (o2 == -1 ? i2 == 1 : (o2 == 1 ? i2 == 0 : true)) &&
+                                          (o3 == -1 ? i3 == 1 : (o3 == 1 ? i3 == 0 : true));
+                        if (comp) {
+                            S += a[i];
+                            K += ku[i];
+                        }
+                    }
+                    const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
+                    const bool self = (o1 == 0 && o2 == 0 && o3 == 0);
+                    const V4<T> q = sm.y[slot][cy0 + o2][cx0 + o1];
+                    if (!self) {
+                        const T w = p.Wex[d] * S;
+                        ex += w * (q.x - f.mx);
+                        ey += w * (q.y - f.my);
+                        ez += w * (q.z - f.mz);
+                    }
+                    pe += p.Wm[d] * K * (p.e0 * q.x + p.e1 * q.y + p.e2 * q.z);
                 }
-                pe += p.Wm[d] * K * (p.e0 * qx + p.e1 * qy + p.e2 * qz);
-            }
+        }
     }
     // -dE / mass: exchange and anisotropy
     T hx = -ex + T(2) * p.e0 * pe;
@@ -147,10 +208,10 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
-            const int cs_ = (n3 - i3 + 2) % 2;
-            cx_ += sm.c[cs_][0][cy0 - i2][cx0 - i1];
-            cy_ += sm.c[cs_][1][cy0 - i2][cx0 - i1];
-            cz_ += sm.c[cs_][2][cy0 - i2][cx0 - i1];
+            const V4<T> v = sm.c[(n3 - i3 + kCellSlots) % kCellSlots][cy0 - i2][cx0 - i1];
+            cx_ += v.x;
+            cy_ += v.y;
+            cz_ += v.z;
         }
     }
     if (p.Msh && (p.terms & NM_ZEE)) {
@@ -193,13 +254,15 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 // STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
 // input.  Block (bx, by, bz) covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [bz*zc, bz*zc+zc).
 template <typename T, bool STAGE>
-__global__ void __launch_bounds__(kTX *kTY) k_node(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ out,
-                                                   T *__restrict__ y_next, StageArgs sa, double t_heff, int zc)
+__global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const T *__restrict__ y,
+                                                        T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
+                                                        double t_heff, int zc)
 {
     if (STAGE && sa.ctl && sa.ctl->done) return;
+    constexpr int TY = kTY<T>;
     __shared__ NodeSmem<T> sm;
     const Geom &g = p.g;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * kTY;
+    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * zc, z1 = min(g.nn3, z0 + zc);
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const int n1 = x0 + tx, n2 = y0 + ty;
@@ -212,19 +275,34 @@ __global__ void __launch_bounds__(kTX *kTY) k_node(LocalParams<T> p, const T *__
         sm.hf[2] = (T)(p.hu2 * su);
         sm.hf[3] = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
     }
+    // copy groups: {node z0-1, node z0, cell z0-1}, then per z the group {node z+1, cell z}
     load_node_plane(p, y, sm, z0 - 1, x0, y0);
     load_node_plane(p, y, sm, z0, x0, y0);
     load_cell_plane(p, sm, z0 - 1, x0, y0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    load_node_plane(p, y, sm, z0 + 1, x0, y0);
+    load_cell_plane(p, sm, z0, x0, y0);
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
     const int ns = (int)g.ns;
     double dt = 0.0;
     if (STAGE) dt = sa.ctl ? sa.ctl->dt : 0.0;
+    // the tile's x-y footprint has all eight cells around every node (uniform material)
+    const bool tile_inner = p.uniform && x0 >= 1 && x0 + kTX <= g.N1 && y0 >= 1 && y0 + TY <= g.N2;
     for (int z = z0; z < z1; ++z) {
-        load_node_plane(p, y, sm, z + 1, x0, y0);
-        load_cell_plane(p, sm, z, x0, y0);
+        // start the copies for the next plane (into the slots of planes z - 2 and cells z - 2, free since
+        // the barrier that ended the previous iteration), then wait for everything but them
+        if (z + 1 < z1) {
+            load_node_plane(p, y, sm, z + 2, x0, y0);
+            load_cell_plane(p, sm, z + 1, x0, y0);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
+        const bool interior = tile_inner && z >= 1 && z <= g.N3 - 1;
         if (active) {
             const int n = (z * g.nn2 + n2) * g.nn1 + n1;
-            const NodeField<T> f = node_field(p, sm, n1, n2, z, n, tx, ty);
+            const NodeField<T> f = interior ? node_field<T, true>(p, sm, n1, n2, z, n, tx, ty)
+                                            : node_field<T, false>(p, sm, n1, n2, z, n, tx, ty);
             if (!STAGE) {
                 out[n] = f.hx;
                 out[ns + n] = f.hy;
@@ -278,7 +356,7 @@ __global__ void __launch_bounds__(kTX *kTY) k_node(LocalParams<T> p, const T *__
 template <typename T>
 static dim3 node_grid(const Geom &g, int *zc)
 {
-    const int bx = div_up(g.nn1, kTX), by = div_up(g.nn2, kTY);
+    const int bx = div_up(g.nn1, kTX), by = div_up(g.nn2, kTY<T>);
     const long bxy = (long)bx * by;
     int chunks = (int)((4L * 152 + bxy - 1) / bxy);
     chunks = chunks < 1 ? 1 : (chunks > g.nn3 ? g.nn3 : chunks);
@@ -291,7 +369,7 @@ void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaSt
 {
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
-    k_node<T, false><<<grid, kTX * kTY, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
+    k_node<T, false><<<grid, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
 }
 
 template <typename T>
@@ -299,7 +377,7 @@ void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, 
 {
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
-    k_node<T, true><<<grid, kTX * kTY, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
+    k_node<T, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
 }
 
 // ---------------------------------------------------------------------------------------------

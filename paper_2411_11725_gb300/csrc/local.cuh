@@ -12,6 +12,11 @@ struct LocalParams {
     Geom g;
     T Wex[8];          // int_cell 2 grad(phi_i).grad(phi_i') for the pattern d (per unit A)
     T Wm[8];           // int_cell phi_i phi_i' for the pattern d
+    // Interior nodes of a uniform material (no cell maps, Ms0 > 0): the 27 assembled weights of the
+    // neighbour offsets o (index (o3+1)*9 + (o2+1)*3 + (o1+1)), exchange (self weight unused) and
+    // anisotropy, and the sum of the exchange weights.  uniform = 0 disables that path.
+    int uniform;
+    T wex27[27], wan27[27], wex_sum;
     T mu0V8;           // mu0 * V / 8
     const T *A;        // cell maps (n_cells) or NULL for the uniform value
     const T *Ku;

@@ -183,6 +183,35 @@ inline LocalParams<T> local_params(nm_mesh M, unsigned terms)
     p.hu_freq = M->hu_freq; p.hu_phase = M->hu_phase;
     p.hc_freq = M->hc_freq; p.hc_phase = M->hc_phase;
     p.terms = terms;
+    // interior weights of a uniform material: each offset o couples through 2^(number of zero components)
+    // cells, all with the same A and Ku
+    p.uniform = (!M->Ms_d && !M->A_d && !M->Ku_d && M->Ms0 > 0.0) ? 1 : 0;
+    {
+        const double A = (terms & NM_EXCH) ? M->A0 : 0.0, Ku = (terms & NM_ANIS) ? M->Ku0 : 0.0;
+        double wsum = 0.0;
+        for (int o3 = -1; o3 <= 1; ++o3)
+            for (int o2 = -1; o2 <= 1; ++o2)
+                for (int o1 = -1; o1 <= 1; ++o1) {
+                    const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
+                    const int cnt = (o1 == 0 ? 2 : 1) * (o2 == 0 ? 2 : 1) * (o3 == 0 ? 2 : 1);
+                    const int k = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
+                    const bool self = o1 == 0 && o2 == 0 && o3 == 0;
+                    double wx = 0.0, wm = V;
+                    for (int kk = 0; kk < 3; ++kk) {
+                        const int dk = (d >> (2 - kk)) & 1;
+                        double v = (dk ? -1.0 : 1.0) / dx[kk];
+                        for (int l = 0; l < 3; ++l)
+                            if (l != kk) v *= dx[l] * (((d >> (2 - l)) & 1) ? 1.0 / 6.0 : 1.0 / 3.0);
+                        wx += v;
+                        wm *= dk ? 1.0 / 6.0 : 1.0 / 3.0;
+                    }
+                    const double we = self ? 0.0 : 2.0 * wx * A * cnt;
+                    p.wex27[k] = (T)we;
+                    p.wan27[k] = (T)(wm * Ku * cnt);
+                    wsum += we;
+                }
+        p.wex_sum = (T)wsum;
+    }
     p.gam = M->gamma / (1.0 + M->alpha * M->alpha);
     p.alpha = M->alpha;
     return p;
