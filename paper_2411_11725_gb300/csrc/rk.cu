@@ -19,7 +19,11 @@ __global__ void k_stage_input(long n_nodes, long ns, const double *__restrict__ 
     for (int c = 0; c < 3; ++c) {
         long i = c * ns + n;
         T acc = 0;
-        for (int j = 0; j < k.n; ++j) acc += (T)k.a[j] * ((const T *)k.p[j])[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= k.n) break;
+            acc += kcoef<T>(k, j) * ((const T *)k.p[j])[i];
+        }
         y[i] = (T)(m[i] + dt * (double)acc);
     }
 }
@@ -64,20 +68,25 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, 
         for (int c = 0; c < 3; ++c) {
             long i = c * ns + n;
             T sb = 0, se = 0;
-            for (int j = 0; j < kb.n; ++j) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j >= kb.n) break;
                 const T kv = ((const T *)kb.p[j])[i];
-                sb += (T)kb.a[j] * kv;
-                se += (T)ke.a[j] * kv;
+                sb += kcoef<T>(kb, j) * kv;
+                se += kcoef<T>(ke, j) * kv;
             }
-            const double m0 = m[i], m5 = m0 + dt * (double)sb;
             if (sizeof(T) == 8) {
+                const double m0 = m[i], m5 = m0 + dt * (double)sb;
                 const double sc = atol + rtol * fmax(fabs(m0), fabs(m5));
                 const double q = dt * (double)se / sc;
                 acc += q * q;
             } else {
-                const T sc = (T)atol + (T)rtol * fmaxf(fabsf((float)m0), fabsf((float)m5));
-                const T q = (T)dt * se / sc;
-                part += q * q;
+                // the error scale only weights the norm: FP32 is ample for max(|m|, |m5|)
+                const float m0 = (float)m[i], dtf = (float)dt;
+                const float m5 = m0 + dtf * (float)sb;
+                const float sc = (float)atol + (float)rtol * fmaxf(fabsf(m0), fabsf(m5));
+                const float q = dtf * (float)se / sc;
+                part += (T)(q * q);
             }
         }
         acc += (double)part;
@@ -141,7 +150,11 @@ __device__ __forceinline__ void advance_node(long n, long ns, const double *__re
     for (int c = 0; c < 3; ++c) {
         long i = c * ns + n;
         T sb = 0;
-        for (int j = 0; j < kb.n; ++j) sb += (T)kb.a[j] * ((const T *)kb.p[j])[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= kb.n) break;
+            sb += kcoef<T>(kb, j) * ((const T *)kb.p[j])[i];
+        }
         v[c] = m[i] + dt * (double)sb;
     }
     if (renorm) {
@@ -309,10 +322,18 @@ __global__ void k_node_volume(Geom g, const double *__restrict__ Ms, double Ms0,
 }
 
 // ---------------------------------------------------------------------------------------------
+// the list with its FP32 coefficients filled in
+static KList fk(const KList &k)
+{
+    KList r = k;
+    for (int j = 0; j < 8; ++j) r.af[j] = (float)k.a[j];
+    return r;
+}
+
 template <typename T>
 void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st)
 {
-    k_stage_input<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, k, ctl, y);
+    k_stage_input<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(k), ctl, y);
 }
 
 int reduction_blocks(long n_nodes)
@@ -326,7 +347,7 @@ void launch_dp5_control(const Geom &g, const double *m, const KList &kb, const K
                         StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st)
 {
     int nb = reduction_blocks(g.n_nodes);
-    k_dp5_err<T><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, kb, ke, inv_mass, ctl, partials);
+    k_dp5_err<T><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), fk(ke), inv_mass, ctl, partials);
     k_dp5_ctl<<<1, 1024, 0, st>>>(partials, nb, n_active, ctl, max_rej);
 }
 
@@ -334,13 +355,13 @@ template <typename T>
 void launch_dp5_update(const Geom &g, double *m, const KList &kb, const T *k7, T *k1, const StepCtl *ctl, int renorm,
                        cudaStream_t st)
 {
-    k_dp5_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, kb, k7, k1, ctl, renorm);
+    k_dp5_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), k7, k1, ctl, renorm);
 }
 
 template <typename T>
 void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, int renorm, cudaStream_t st)
 {
-    k_rk4_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, kb, ctl, renorm);
+    k_rk4_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), ctl, renorm);
     k_rk4_advance<<<1, 1, 0, st>>>(ctl);
 }
 

@@ -10,7 +10,16 @@ struct KList {
     const void *p[8];
     double a[8];
     int n;
+    float af[8];  // a in FP32 (filled by the launch functions; used by the FP32 path)
 };
+
+// coefficient j of a slope list in the working precision
+template <typename T>
+__device__ __forceinline__ T kcoef(const KList &k, int j)
+{
+    if constexpr (sizeof(T) == 4) return k.af[j];
+    else return (T)k.a[j];
+}
 
 int reduction_blocks(long n_nodes);
 
