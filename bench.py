@@ -148,20 +148,23 @@ def algorithmic_bytes(name, stage, n, b, with_maps):
         return 2 * 3 * c * X * N2 + 6 * b * X * H2
     if name == "demag_x_inv":
         return 3 * c * X * N2 * N3 + ms + 3 * b * Nc
+    # stage inputs and the error scale read the FP64 m (24 B/node), or in the FP32 path its FP32 copy
+    mb = 3 * b if b == 4 else 24
     if name == "node_llg_stage":
-        # y_s, Ms*H_c, 1/mass in; k_s out; for s < 7 also m (FP64), the k_j with non-zero a_{s+1,j}
+        # y_s, Ms*H_c, 1/mass in; k_s out; for s < 7 also m, the k_j with non-zero a_{s+1,j}
         # (j < s), and y_{s+1} out
         base = 3 * b * Nn + 3 * b * Nc + b * Nn + 3 * b * Nn
         if stage < 7:
             nk = {2: 1, 3: 2, 4: 3, 5: 4, 6: 4}[stage]
-            base += 24 * Nn + nk * 3 * b * Nn + 3 * b * Nn
+            base += mb * Nn + nk * 3 * b * Nn + 3 * b * Nn
         return base
     if name == "stage_input":
-        return 24 * Nn + 3 * b * Nn + 3 * b * Nn
+        return mb * Nn + 3 * b * Nn + 3 * b * Nn
     if name == "dp5_error_control":
-        return 24 * Nn + 6 * 3 * b * Nn + b * Nn
+        return mb * Nn + 6 * 3 * b * Nn + b * Nn
     if name == "dp5_update":
-        return 24 * Nn + 6 * 3 * b * Nn + 24 * Nn + 3 * b * Nn
+        # m in and out (FP64), b_j k_j (j = 1, 3..6) and k7 in, k1 <- k7 out, FP32 copy of m out
+        return 24 * Nn + 6 * 3 * b * Nn + 24 * Nn + 3 * b * Nn + (3 * b * Nn if b == 4 else 0)
     return 0
 
 

@@ -330,6 +330,24 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
     int rc = ensure_vjp_buffers<T>(M);
     if (rc) return rc;
     const Tableau tb = tableau(method);
+    // The forward steps and their recomputation in the reverse sweep must follow the same arithmetic,
+    // and the reverse sweep restores m from checkpoints: stage inputs are formed from the FP64 m during
+    // this call (no FP32 copy of m), and the step graphs are recaptured around it.
+    struct MfOff {
+        nm_mesh M;
+        float *mf;
+        explicit MfOff(nm_mesh m) : M(m), mf(m->mf)
+        {
+            M->mf = nullptr;
+            free_graphs(M);
+        }
+        ~MfOff()
+        {
+            M->mf = mf;
+            M->mf_valid = false;
+            free_graphs(M);
+        }
+    } mf_off(M);
     // workspaces of this call (stream-ordered, freed at the end)
     std::vector<void *> owned;
     auto galloc = [&](void **p, size_t bytes) -> int {

@@ -71,6 +71,7 @@ static long footprint(const Geom &g, int prec)
     long rs = prec == NM_F64 ? 8 : 4;
     long b = 0;
     b += 3 * g.ns * 8;            // m
+    if (prec == NM_F32) b += 3 * g.ns * 4;  // FP32 copy of m
     b += 2 * 3 * g.ns * rs;       // y ping-pong
     b += 7 * 3 * g.ns * rs;       // k1..k7
     b += 2 * 3 * g.ns * rs;       // h_eff in/out staging
@@ -116,7 +117,7 @@ static void release(nm_mesh M)
     if (!M) return;
     cudaStreamSynchronize(M->st);
     free_graphs(M);
-    void *ptrs[] = {M->m, M->y[0], M->y[1], M->hin, M->hout, M->inv_mass, M->vol, M->MsH, M->S, M->Nk, M->tw,
+    void *ptrs[] = {M->m, M->mf, M->y[0], M->y[1], M->hin, M->hout, M->inv_mass, M->vol, M->MsH, M->S, M->Nk, M->tw,
                     M->tw64, M->A_d, M->Ku_d, M->Ms_d, M->Ms64_d, M->Msh_d, M->hcell64_d, M->ctl, M->partials,
                     M->mean_d, M->n_active_d, M->vj_w, M->vj_h, M->vj_q, M->vj_g, M->vj_H, M->vj_HW, M->vj_M,
                     M->vj_gMs};
@@ -195,6 +196,7 @@ int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int 
         return rc;                                       \
     }
     ALLOC(M->m, 3 * g.ns * 8);
+    if (precision == NM_F32) ALLOC(M->mf, 3 * g.ns * 4);
     ALLOC(M->y[0], 3 * g.ns * rs);
     ALLOC(M->y[1], 3 * g.ns * rs);
     for (int i = 0; i < 7; ++i) ALLOC(M->k[i], 3 * g.ns * rs);
@@ -501,6 +503,16 @@ extern "C" int nm_set_state(nm_mesh M, const double *m, int where, double t, dou
     CUDA_TRY(cudaMemcpyAsync(M->ctl, h, sizeof(StepCtl), cudaMemcpyHostToDevice, M->st));
     M->state_set = true;
     M->k1_valid = false;
+    M->mf_valid = false;
+    return NM_OK;
+}
+
+int ensure_mf(nm_mesh M)
+{
+    if (!M->mf || M->mf_valid) return NM_OK;
+    launch_convert<double, float>(3 * M->g.ns, M->m, M->mf, M->st);
+    CHECK_LAUNCH();
+    M->mf_valid = true;
     return NM_OK;
 }
 
@@ -594,6 +606,7 @@ static void enqueue_stage(nm_mesh M, const LocalParams<T> &p, int s, double c_s,
     }
     StageArgs sa{};
     sa.m = M->m;
+    sa.mf = M->mf;
     for (int j = 0; j < 7; ++j) sa.k[j] = M->k[j];
     for (int j = 0; j < n_next; ++j) {
         sa.a[j] = a_next[j];
@@ -612,7 +625,7 @@ static void enqueue_k1(nm_mesh M)
 {
     const LocalParams<T> p = local_params<T>(M, M->terms);
     KList none{};
-    launch_stage_input<T>(M->g, M->m, none, M->ctl, (T *)M->y[0], M->st);
+    launch_stage_input<T>(M->g, M->m, none, M->ctl, (T *)M->y[0], M->st, M->mf);
     enqueue_stage<T>(M, p, 1, 0.0, (const T *)M->y[0], nullptr, nullptr, 0);
 }
 
@@ -625,7 +638,7 @@ static void enqueue_dp5_step(nm_mesh M)
     k2in.p[0] = M->k[0];
     k2in.a[0] = kDpA[1][0];
     k2in.n = 1;
-    launch_stage_input<T>(g, M->m, k2in, M->ctl, (T *)M->y[0], M->st);  // y_2
+    launch_stage_input<T>(g, M->m, k2in, M->ctl, (T *)M->y[0], M->st, M->mf);  // y_2
     marker(M)("stage_input");
     for (int s = 2; s <= 7; ++s) {
         const T *ys = (const T *)M->y[s % 2];
@@ -641,11 +654,11 @@ static void enqueue_dp5_step(nm_mesh M)
     }
     kb.n = ke.n = 6;
     launch_dp5_control<T>(g, M->m, kb, ke, (const T *)M->inv_mass, M->ctl, M->partials, M->n_active, M->max_rej,
-                          M->st);
+                          M->st, M->mf);
     marker(M)("dp5_error_control");
     KList ku = kb;
     ku.n = 5;  // b7 = 0
-    launch_dp5_update<T>(g, M->m, ku, (const T *)M->k[6], (T *)M->k[0], M->ctl, M->renorm, M->st);
+    launch_dp5_update<T>(g, M->m, ku, (const T *)M->k[6], (T *)M->k[0], M->ctl, M->renorm, M->st, M->mf);
     marker(M)("dp5_update");
 }
 
@@ -655,7 +668,7 @@ static void enqueue_rk4_step(nm_mesh M)
     const LocalParams<T> p = local_params<T>(M, M->terms);
     const Geom &g = M->g;
     KList none{};
-    launch_stage_input<T>(g, M->m, none, M->ctl, (T *)M->y[1], M->st);  // y_1 = m
+    launch_stage_input<T>(g, M->m, none, M->ctl, (T *)M->y[1], M->st, M->mf);  // y_1 = m
     marker(M)("stage_input");
     for (int s = 1; s <= 4; ++s) {
         const T *ys = (const T *)M->y[s % 2];
@@ -668,7 +681,7 @@ static void enqueue_rk4_step(nm_mesh M)
         kb.a[j] = kRk4B[j];
     }
     kb.n = 4;
-    launch_rk4_update<T>(g, M->m, kb, M->ctl, M->renorm, M->st);
+    launch_rk4_update<T>(g, M->m, kb, M->ctl, M->renorm, M->st, M->mf);
     marker(M)("rk4_update");
 }
 
@@ -687,6 +700,8 @@ static int enqueue_step(nm_mesh M, int method)
 
 int launch_step(nm_mesh M, int method)
 {
+    int rc0 = ensure_mf(M);
+    if (rc0) return rc0;
     cudaGraphExec_t &gx = M->graph[method];
     if (!gx) {
         cudaGraph_t graph;
@@ -709,6 +724,8 @@ int launch_step(nm_mesh M, int method)
 int ensure_k1(nm_mesh M, int method)
 {
     if (method != NM_DP54 || M->k1_valid) return NM_OK;
+    int rc0 = ensure_mf(M);
+    if (rc0) return rc0;
     if (M->prec == NM_F64) enqueue_k1<double>(M);
     else enqueue_k1<float>(M);
     CHECK_LAUNCH();

@@ -327,7 +327,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
                 out[2 * ns + n] = kz;
                 if (y_next) {
                     // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working
-                    // precision, the addition to the FP64 magnetisation in FP64
+                    // precision
                     T ax = 0, ay = 0, az = 0;
 #pragma unroll
                     for (int j = 0; j < 7; ++j) {
@@ -343,9 +343,17 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
                     ax += as * kx;
                     ay += as * ky;
                     az += as * kz;
-                    y_next[n] = (T)(sa.m[n] + dt * (double)ax);
-                    y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)ay);
-                    y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)az);
+                    if (sizeof(T) == 4 && sa.mf) {
+                        // FP32 path: y_{s+1} is an FP32 quantity, formed from the FP32 copy of m
+                        const float dtf = (float)dt;
+                        y_next[n] = (T)(sa.mf[n] + dtf * (float)ax);
+                        y_next[ns + n] = (T)(sa.mf[ns + n] + dtf * (float)ay);
+                        y_next[2 * ns + n] = (T)(sa.mf[2 * ns + n] + dtf * (float)az);
+                    } else {
+                        y_next[n] = (T)(sa.m[n] + dt * (double)ax);
+                        y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)ay);
+                        y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)az);
+                    }
                 }
             }
         }

@@ -39,6 +39,7 @@ struct LocalParams {
 //   y_next:  next stage input y_{s+1} = m + dt sum_{j<=s} a_j k_j (3 x ns), when non-NULL
 struct StageArgs {
     const double *m;          // FP64 master magnetisation (3 x ns)
+    const float *mf;          // its FP32 copy (FP32 path; NULL = form the next input from m in FP64)
     const void *k[8];         // k_1 .. k_s (k[s-1] is the one being written)
     double a[8];              // a_{s+1, j}, j = 1 .. s
     int s;                    // stage index (1-based) of the slope being computed

@@ -58,6 +58,8 @@ struct nm_mesh_s {
     double dx[3];
     // device buffers
     double *m = nullptr;
+    float *mf = nullptr;     // FP32 copy of m (FP32 meshes): kept equal to fl32(m) by the step updates
+    bool mf_valid = false;   // false after m changed outside the step graphs
     void *y[2] = {nullptr, nullptr};
     void *k[7] = {};
     void *hin = nullptr, *hout = nullptr;
@@ -113,6 +115,7 @@ int push_ctl(nm_mesh M);
 void free_graphs(nm_mesh M);
 int check_step_args(nm_mesh M, int method, double rtol, double atol);
 int launch_step(nm_mesh M, int method);  // one step attempt of the captured step graph
+int ensure_mf(nm_mesh M);                // refresh the FP32 copy of m if m changed outside the steps
 int ensure_k1(nm_mesh M, int method);    // FSAL slope at the resident state when not valid
 
 // device buffer owned by the mesh (freed with it)

@@ -8,9 +8,10 @@ namespace nm {
 constexpr int kRedThreads = 256;
 
 // y = m + dt * sum_j a_j k_j: slope combination in the working precision, addition in FP64
+// (with mf, the FP32 path forms y = fl32(m) + dt * sum in FP32: y is an FP32 quantity either way)
 template <typename T>
 __global__ void k_stage_input(long n_nodes, long ns, const double *__restrict__ m, KList k, const StepCtl *ctl,
-                              T *__restrict__ y)
+                              T *__restrict__ y, const float *__restrict__ mf)
 {
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
@@ -24,7 +25,8 @@ __global__ void k_stage_input(long n_nodes, long ns, const double *__restrict__ 
             if (j >= k.n) break;
             acc += kcoef<T>(k, j) * ((const T *)k.p[j])[i];
         }
-        y[i] = (T)(m[i] + dt * (double)acc);
+        if (sizeof(T) == 4 && mf) y[i] = (T)(mf[i] + (float)dt * (float)acc);
+        else y[i] = (T)(m[i] + dt * (double)acc);
     }
 }
 
@@ -56,14 +58,17 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 template <typename T>
 __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, const double *__restrict__ m,
                                                           KList kb, KList ke, const T *__restrict__ inv_mass,
-                                                          const StepCtl *ctl, double *partials)
+                                                          const StepCtl *ctl, double *partials,
+                                                          const float *__restrict__ mf)
 {
     __shared__ double sh[kRedThreads];
     if (ctl->done) return;
     const double dt = ctl->dt, rtol = ctl->rtol, atol = ctl->atol;
     double acc = 0.0;
+    // no early exit per node: all loads of an iteration are independent, so they are in flight together
+#pragma unroll 2
     for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < n_nodes; n += (long)gridDim.x * blockDim.x) {
-        if (!(inv_mass[n] > T(0))) continue;
+        const bool magnetic = inv_mass[n] > T(0);
         T part = 0;
         for (int c = 0; c < 3; ++c) {
             long i = c * ns + n;
@@ -79,17 +84,17 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, 
                 const double m0 = m[i], m5 = m0 + dt * (double)sb;
                 const double sc = atol + rtol * fmax(fabs(m0), fabs(m5));
                 const double q = dt * (double)se / sc;
-                acc += q * q;
+                acc += magnetic ? q * q : 0.0;
             } else {
                 // the error scale only weights the norm: FP32 is ample for max(|m|, |m5|)
-                const float m0 = (float)m[i], dtf = (float)dt;
+                const float m0 = mf ? mf[i] : (float)m[i], dtf = (float)dt;
                 const float m5 = m0 + dtf * (float)sb;
                 const float sc = (float)atol + (float)rtol * fmaxf(fabsf(m0), fabsf(m5));
                 const float q = dtf * (float)se / sc;
                 part += (T)(q * q);
             }
         }
-        acc += (double)part;
+        if (sizeof(T) == 4 && magnetic) acc += (double)part;
     }
     double s = block_sum<T>(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -169,7 +174,7 @@ __device__ __forceinline__ void advance_node(long n, long ns, const double *__re
 // Accepted step: m <- m5 (optionally renormalised), k1 <- k7 (FSAL).  Rejected: nothing.
 template <typename T>
 __global__ void k_dp5_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const T *__restrict__ k7,
-                             T *__restrict__ k1, const StepCtl *ctl, int renorm)
+                             T *__restrict__ k1, const StepCtl *ctl, int renorm, float *__restrict__ mf)
 {
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
@@ -179,20 +184,25 @@ __global__ void k_dp5_update(long n_nodes, long ns, double *__restrict__ m, KLis
     for (int c = 0; c < 3; ++c) {
         long i = c * ns + n;
         m[i] = v[c];
+        if (mf) mf[i] = (float)v[c];
         k1[i] = k7[i];
     }
 }
 
 // RK4 end of step: m <- m + dt/6 (k1 + 2 k2 + 2 k3 + k4), optional renormalisation.
 template <typename T>
-__global__ void k_rk4_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const StepCtl *ctl, int renorm)
+__global__ void k_rk4_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const StepCtl *ctl, int renorm,
+                             float *__restrict__ mf)
 {
     long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
     if (n >= n_nodes) return;
     if (ctl->done) return;
     double v[3];
     advance_node<T>(n, ns, m, kb, ctl->dt, renorm, v);
-    for (int c = 0; c < 3; ++c) m[c * ns + n] = v[c];
+    for (int c = 0; c < 3; ++c) {
+        m[c * ns + n] = v[c];
+        if (mf) mf[c * ns + n] = (float)v[c];
+    }
 }
 
 __global__ void k_rk4_advance(StepCtl *ctl)
@@ -331,9 +341,10 @@ static KList fk(const KList &k)
 }
 
 template <typename T>
-void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st)
+void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st,
+                        const float *mf)
 {
-    k_stage_input<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(k), ctl, y);
+    k_stage_input<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(k), ctl, y, mf);
 }
 
 int reduction_blocks(long n_nodes)
@@ -344,24 +355,28 @@ int reduction_blocks(long n_nodes)
 
 template <typename T>
 void launch_dp5_control(const Geom &g, const double *m, const KList &kb, const KList &ke, const T *inv_mass,
-                        StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st)
+                        StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st,
+                        const float *mf)
 {
-    int nb = reduction_blocks(g.n_nodes);
-    k_dp5_err<T><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), fk(ke), inv_mass, ctl, partials);
+    // up to 4096 partial sums (the mesh's partials buffer), so that enough loads are in flight
+    long nbl = (g.n_nodes + kRedThreads - 1) / kRedThreads;
+    const int nb = (int)(nbl > 4096 ? 4096 : (nbl < 1 ? 1 : nbl));
+    k_dp5_err<T><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), fk(ke), inv_mass, ctl, partials, mf);
     k_dp5_ctl<<<1, 1024, 0, st>>>(partials, nb, n_active, ctl, max_rej);
 }
 
 template <typename T>
 void launch_dp5_update(const Geom &g, double *m, const KList &kb, const T *k7, T *k1, const StepCtl *ctl, int renorm,
-                       cudaStream_t st)
+                       cudaStream_t st, float *mf)
 {
-    k_dp5_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), k7, k1, ctl, renorm);
+    k_dp5_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), k7, k1, ctl, renorm, mf);
 }
 
 template <typename T>
-void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, int renorm, cudaStream_t st)
+void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, int renorm, cudaStream_t st,
+                       float *mf)
 {
-    k_rk4_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), ctl, renorm);
+    k_rk4_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), ctl, renorm, mf);
     k_rk4_advance<<<1, 1, 0, st>>>(ctl);
 }
 
@@ -406,12 +421,12 @@ void launch_node_volume(const Geom &g, const double *Ms, double Ms0, double V, T
 
 #define NM_INST(T)                                                                                             \
     template void launch_stage_input<T>(const Geom &, const double *, const KList &, const StepCtl *, T *,       \
-                                        cudaStream_t);                                                         \
+                                        cudaStream_t, const float *);                                                         \
     template void launch_dp5_control<T>(const Geom &, const double *, const KList &, const KList &, const T *,   \
-                                        StepCtl *, double *, double, int, cudaStream_t);                       \
+                                        StepCtl *, double *, double, int, cudaStream_t, const float *);                       \
     template void launch_dp5_update<T>(const Geom &, double *, const KList &, const T *, T *, const StepCtl *,  \
-                                       int, cudaStream_t);                                                     \
-    template void launch_rk4_update<T>(const Geom &, double *, const KList &, StepCtl *, int, cudaStream_t);    \
+                                       int, cudaStream_t, float *);                                                     \
+    template void launch_rk4_update<T>(const Geom &, double *, const KList &, StepCtl *, int, cudaStream_t, float *);    \
     template void launch_mean<T>(const Geom &, const double *, const T *, double *, double *, cudaStream_t);     \
     template void launch_cells_to_internal<T>(const Geom &, const double *, int, double, const double *, T *,  \
                                               cudaStream_t);                                                   \

@@ -23,16 +23,21 @@ __device__ __forceinline__ T kcoef(const KList &k, int j)
 
 int reduction_blocks(long n_nodes);
 
+// mf: FP32 copy of m (FP32 path; NULL = use m).  Stage inputs and the error scale read it; the updates
+// keep it equal to fl32(m).
 template <typename T>
-void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st);
+void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st,
+                        const float *mf = nullptr);
 template <typename T>
 void launch_dp5_control(const Geom &g, const double *m, const KList &kb, const KList &ke, const T *inv_mass,
-                        StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st);
+                        StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st,
+                        const float *mf = nullptr);
 template <typename T>
 void launch_dp5_update(const Geom &g, double *m, const KList &kb, const T *k7, T *k1, const StepCtl *ctl, int renorm,
-                       cudaStream_t st);
+                       cudaStream_t st, float *mf = nullptr);
 template <typename T>
-void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, int renorm, cudaStream_t st);
+void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, int renorm, cudaStream_t st,
+                       float *mf = nullptr);
 template <typename T>
 void launch_mean(const Geom &g, const double *m, const T *vol, double *partials, double *out, cudaStream_t st);
 template <typename Tin, typename Tout>
