@@ -170,7 +170,7 @@ def algorithmic_bytes(name, stage, n, b, with_maps):
 
 def traffic_for(name, workload_key):
     """dram bytes per launch from the committed ncu summary, if it matches the current kernels."""
-    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
     try:
         with open(p) as f:
             d = json.load(f)
