@@ -21,6 +21,9 @@ template <typename T, int LG = 0>
 constexpr int kMaxThreads = (sizeof(T) == 4 && LG >= 11) ? 1024 : 512;
 template <typename T, int LG = 0>
 constexpr int kMinBlocks = (sizeof(T) == 4 && LG < 11) ? 2 : 1;
+// values per thread per FFT stage in the y passes: radix-16 stages for the long FP32 lines
+template <typename T, int LG>
+constexpr int kYEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
 // the single-layer pass keeps up to 1024 threads (FP32) so that long y lines still fit one block
 template <typename T>
 constexpr int kMaxThreadsYC = sizeof(T) == 4 ? 1024 : 512;
@@ -256,7 +259,8 @@ __global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geo
     cpa_wait_all();
     __syncthreads();
     auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    f3::fft<T, LG, DIR, true, true, false>(buf, G, FastDiv((unsigned)G), b.tw, g.twlg, nin, nout, f3::NoFn<T>(), dst);
+    f3::fft<T, LG, DIR, true, true, false, kYEpt<T, LG>>(buf, G, FastDiv((unsigned)G), b.tw, g.twlg, nin, nout,
+                                                         f3::NoFn<T>(), dst);
 }
 
 // The six real tensor components at octant frequency (kx, a2, kz), with the sign of the odd ones in
@@ -476,12 +480,13 @@ DemagPlan demag_plan(const Geom &g)
         p.x_smem = 0;
     }
     if (g.N3 > 1) {
-        const long ybudget = 8L * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 1024 : 512);
+        const int yept = (sizeof(T) == 4 && g.lgP2 >= 10) ? 16 : 8;
+        const long ybudget = (long)yept * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 1024 : 512);
         int G = pow2_floor(ybudget / g.P2);
         G = G > 16 ? 16 : G;
         if (G < 1 || g.lgP2 > 11) p.ok = false;
         p.y_G = G < 1 ? 1 : G;
-        p.y_threads = threads_for((long)p.y_G * g.P2);
+        p.y_threads = threads_for((long)p.y_G * g.P2 * 8 / yept);
         p.y_smem = (size_t)p.y_G * g.P2 * cs;
         int Gz = Gmin > 16 ? 16 : Gmin, KY = 0;
         while (Gz >= 1 && (KY = pow2_floor(budget / (6L * Gz * g.P3))) < 1) Gz /= 2;

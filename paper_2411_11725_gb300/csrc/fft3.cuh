@@ -1,8 +1,8 @@
 // Block-level power-of-two FFT engine with the transform length fixed at compile time.
 //
-// A length-2^LG transform runs as Stockham stages: a first stage of radix 2^(LG mod 3) (radix 8 when
-// LG is a multiple of 3), then radix-8 stages.  Each thread keeps 8 complex values in registers per
-// stage (one radix-8 butterfly, or several smaller ones).  Because LG, the radices, the sub-transform
+// A length-2^LG transform runs as Stockham stages: a first stage of the remainder radix, then radix-8
+// (or radix-16) stages.  Each thread keeps 8 (or 16) complex values in registers per stage (one
+// butterfly of the largest radix, or several smaller ones).  Because LG, the radices, the sub-transform
 // lengths and the direction are template constants, every index of a stage reduces to shifts, masks
 // and immediate offsets.  The first stage reads its inputs through a caller functor or from shared
 // memory, and the last stage writes through a functor or to shared memory; only the exchanges between
@@ -22,10 +22,15 @@
 namespace nm {
 namespace f3 {
 
-__host__ __device__ constexpr int first_lg(int LG) { return LG % 3 == 0 ? 3 : LG % 3; }
-__host__ __device__ constexpr int n_stages(int LG) { return LG == 0 ? 0 : 1 + (LG - first_lg(LG)) / 3; }
-__host__ __device__ constexpr int stage_lg(int LG, int s) { return s == 0 ? first_lg(LG) : 3; }
-__host__ __device__ constexpr int stage_slg(int LG, int s) { return s == 0 ? 0 : first_lg(LG) + 3 * (s - 1); }
+// Stage plan of a length-2^LG transform with at most 2^RM values per butterfly (RM = 3: radix 8,
+// RM = 4: radix 16): the remainder radix first, then radix 2^RM.
+__host__ __device__ constexpr int first_lg(int LG, int RM = 3) { return LG % RM == 0 ? RM : LG % RM; }
+__host__ __device__ constexpr int n_stages(int LG, int RM = 3) { return LG == 0 ? 0 : 1 + (LG - first_lg(LG, RM)) / RM; }
+__host__ __device__ constexpr int stage_lg(int LG, int s, int RM = 3) { return s == 0 ? first_lg(LG, RM) : RM; }
+__host__ __device__ constexpr int stage_slg(int LG, int s, int RM = 3)
+{
+    return s == 0 ? 0 : first_lg(LG, RM) + RM * (s - 1);
+}
 
 __host__ __device__ constexpr int pad16c(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int padded(int L) { return L + (L >> 4) + 1; }
@@ -94,14 +99,15 @@ enum { IN_FN = 0, IN_SM = 1 };
 enum { OUT_FN = 0, OUT_SM = 1 };
 
 // One stage S of a length-2^LG transform on nl lines (nb = nl * 2^LG / R butterflies).
-template <typename T, int LG, int S, int DIR, bool LF, int IN, int OUT, bool SYNC_IN, bool SYNC_OUT, typename Src,
-          typename Dst>
+template <typename T, int LG, int S, int DIR, bool LF, int IN, int OUT, bool SYNC_IN, bool SYNC_OUT, int EPT,
+          typename Src, typename Dst>
 __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl, const FastDiv &nlf,
                                       const Cx<T> *__restrict__ tw, int twlg, int nin, int nout, const Src &src,
                                       const Dst &dst)
 {
-    constexpr int RLG = stage_lg(LG, S), R = 1 << RLG, SLG = stage_slg(LG, S), NS = 1 << SLG;
-    constexpr int L = 1 << LG, LR = L >> RLG, LSZ = padded(L), BPT = 8 / R;
+    constexpr int RM = EPT == 16 ? 4 : 3;
+    constexpr int RLG = stage_lg(LG, S, RM), R = 1 << RLG, SLG = stage_slg(LG, S, RM), NS = 1 << SLG;
+    constexpr int L = 1 << LG, LR = L >> RLG, LSZ = padded(L), BPT = EPT / R;
     const int nb = nl * LR;
     Cx<T> v[BPT][R];
     int jv[BPT], lv[BPT];
@@ -184,20 +190,20 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl, const Fas
     if (SYNC_OUT) __syncthreads();
 }
 
-template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, typename Src, typename Dst>
+template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT, typename Src, typename Dst>
 __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw,
                                            int twlg, int nin, int nout, const Src &src, const Dst &dst)
 {
-    constexpr int NSG = n_stages(LG);
+    constexpr int NSG = n_stages(LG, EPT == 16 ? 4 : 3);
     if constexpr (S < NSG) {
         constexpr bool first = S == 0, last = S + 1 == NSG;
         constexpr int IN = (first && !SRC_SM) ? IN_FN : IN_SM;
         constexpr int OUT = (last && !DST_SM) ? OUT_FN : OUT_SM;
         constexpr bool SYNC_IN = IN == IN_SM && OUT == OUT_SM;  // in place: all reads before any write
         constexpr bool SYNC_OUT = OUT == OUT_SM;
-        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT>(buf, nl, nlf, tw, twlg, first ? nin : (1 << LG),
-                                                          last ? nout : (1 << LG), src, dst);
-        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT, EPT>(buf, nl, nlf, tw, twlg, first ? nin : (1 << LG),
+                                                               last ? nout : (1 << LG), src, dst);
+        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM, EPT>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
     }
 }
 
@@ -205,13 +211,14 @@ __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nl
 // SRC_SM: the first stage reads the shared layout (the caller synchronised after filling it);
 // otherwise src(l, i) is called for i < nin.  DST_SM: the last stage writes the shared layout
 // (followed by a barrier); otherwise dst(l, o, v) is called for o < nout.
-// Needs nl * 2^LG <= 8 * blockDim.x.
-template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, typename Src, typename Dst>
+// EPT (8 or 16) values per thread per stage: needs nl * 2^LG <= EPT * blockDim.x.
+template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT = 8, typename Src, typename Dst>
 __device__ __forceinline__ void fft(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw, int twlg,
                                     int nin, int nout, const Src &src, const Dst &dst)
 {
     static_assert(LG >= 1, "length-1 transforms are copies");
-    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+    static_assert(EPT == 8 || EPT == 16, "8 or 16 values per thread");
+    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM, EPT>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
 }
 
 // placeholder functor for a stage side that is shared memory
