@@ -24,6 +24,13 @@ constexpr int kMinBlocks = (sizeof(T) == 4 && LG < 11) ? 2 : 1;
 // values per thread per FFT stage in the y passes: radix-16 stages for the long FP32 lines
 template <typename T, int LG>
 constexpr int kYEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
+// z pass: 16 values per thread for short FP32 lines (up to 32), so that a block spans 16 kx columns
+// (128-byte rows); longer lines keep 8 (measured faster)
+template <typename T, int LG>
+constexpr int kZEpt = (sizeof(T) == 4 && LG <= 5) ? 16 : 8;
+// forward x pass: radix-16 stages for FP32 lines of 2^10 complex values (the inverse keeps 8: measured)
+template <typename T, int LG>
+constexpr int kXEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
 // the single-layer pass keeps up to 1024 threads (FP32) so that long y lines still fit one block
 template <typename T>
 constexpr int kMaxThreadsYC = sizeof(T) == 4 ? 1024 : 512;
@@ -119,7 +126,8 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 3 : 2)
         if (CELL_IN) return cx<T>(p[0], x + 1 < N1 ? p[1] : T(0));
         return cell_M_pair<T>(p, nn1, plane, Ms, Ms0, xi.cell + x, x + 1 < N1);
     };
-    f3::fft<T, LG, -1, false, false, true>(buf, nl, FastDiv(1u), b.tw, g.twlg, (N1 + 1) >> 1, Q, src, f3::NoFn<T>());
+    f3::fft<T, LG, -1, false, false, true, kXEpt<T, LG>>(buf, nl, FastDiv(1u), b.tw, g.twlg, (N1 + 1) >> 1, Q, src,
+                                                         f3::NoFn<T>());
     // X_k = (Z_k + conj Z_{Q-k})/2 - (i/2) W^k (Z_k - conj Z_{Q-k}),  W = e^{-2 pi i / P1},  k = 0..Q;
     // thread (l, k) with k < Q/2 writes X_k and X_{Q-k}; k = 0 also writes X_{Q/2} (and X_0, X_Q)
     const int wsh = g.twlg - (LG + 1);
@@ -330,7 +338,8 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
         __syncthreads();
     }
     const FastDiv nlf((unsigned)nl);
-    f3::fft<T, LG, -1, true, true, true>(buf, nl, nlf, b.tw, g.twlg, g.N3, P3, f3::NoFn<T>(), f3::NoFn<T>());
+    f3::fft<T, LG, -1, true, true, true, kZEpt<T, LG>>(buf, nl, nlf, b.tw, g.twlg, g.N3, P3, f3::NoFn<T>(),
+                                                    f3::NoFn<T>());
     const int npts = KY * G * P3;
     const int lG = __ffs(G) - 1, lKY = __ffs(KY) - 1;
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
@@ -351,7 +360,7 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
         const int ky = row_ky(r);
         if (ky >= 0) b.S[gaddr(c, ky, z) + gg] = v;
     };
-    f3::fft<T, LG, +1, true, true, false>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
+    f3::fft<T, LG, +1, true, true, false, kZEpt<T, LG>>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
 }
 
 // Single-layer variant (N3 == 1, P3 == 1): forward y, tensor product at kz = 0 (each octant row a2
@@ -468,14 +477,22 @@ DemagPlan demag_plan(const Geom &g)
     const long budget = 8L * kMaxThreads<T>;
     const int Gmin = (int)(64 / cs);
     if (g.P1 > 1) {
-        int lpb = (int)(8L * kXThreads / g.Q);
+        const int xept = (sizeof(T) == 4 && g.lgQ >= 10) ? 16 : 8;
+        int lpb = (int)((long)xept * kXThreads / g.Q);
         lpb = lpb > 64 ? 64 : lpb;
         if (lpb < 1 || g.lgQ > 10) p.ok = false;
         p.x_lpb = lpb < 1 ? 1 : lpb;
         p.x_threads = kXThreads;
         p.x_smem = (size_t)p.x_lpb * f3::padded(g.Q) * cs + (size_t)p.x_lpb * 3 * sizeof(int);
+        int lpbi = (int)(8L * kXThreads / g.Q);  // the inverse transform keeps 8 values per thread
+        lpbi = lpbi > 64 ? 64 : lpbi;
+        if (lpbi < 1) p.ok = false;
+        p.xi_lpb = lpbi < 1 ? 1 : lpbi;
+        p.xi_smem = (size_t)p.xi_lpb * f3::padded(g.Q) * cs + (size_t)p.xi_lpb * 3 * sizeof(int);
     } else {
         p.x_lpb = 1;
+        p.xi_lpb = 1;
+        p.xi_smem = 0;
         p.x_threads = 256;
         p.x_smem = 0;
     }
@@ -488,8 +505,10 @@ DemagPlan demag_plan(const Geom &g)
         p.y_G = G < 1 ? 1 : G;
         p.y_threads = threads_for((long)p.y_G * g.P2 * 8 / yept);
         p.y_smem = (size_t)p.y_G * g.P2 * cs;
-        int Gz = Gmin > 16 ? 16 : Gmin, KY = 0;
-        while (Gz >= 1 && (KY = pow2_floor(budget / (6L * Gz * g.P3))) < 1) Gz /= 2;
+        const int zept = (sizeof(T) == 4 && g.lgP3 <= 5) ? 16 : 8;
+        const long zbudget = (long)zept * kMaxThreads<T>;
+        int Gz = zept == 16 ? 16 : Gmin, KY = 0;
+        while (Gz >= 1 && (KY = pow2_floor(zbudget / (6L * Gz * g.P3))) < 1) Gz /= 2;
         if (Gz < 1 || KY < 1 || g.lgP3 > 7) p.ok = false;
         Gz = Gz < 1 ? 1 : Gz;
         KY = KY < 1 ? 1 : KY;
@@ -497,7 +516,7 @@ DemagPlan demag_plan(const Geom &g)
         KY = KY > kyc ? kyc : KY;
         p.z_G = Gz;
         p.z_KY = KY;
-        p.z_threads = threads_for(6L * KY * Gz * g.P3);
+        p.z_threads = threads_for(6L * KY * Gz * g.P3 * 8 / zept);
         p.z_smem = (size_t)6 * KY * Gz * g.P3 * cs;
     } else {
         int G = pow2_floor(8L * kMaxThreadsYC<T> / (3L * g.P2));
@@ -507,10 +526,25 @@ DemagPlan demag_plan(const Geom &g)
         p.yc_threads = threads_for(3L * p.yc_G * g.P2);
         p.yc_smem = (size_t)3 * p.yc_G * g.P2 * cs;
     }
+    // every block holds at most (values per thread) x (threads) values of its transforms
+    if (g.P1 > 1) {
+        const long xept = (sizeof(T) == 4 && g.lgQ >= 10) ? 16 : 8;
+        if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > 8L * p.x_threads) p.ok = false;
+    }
+    if (g.N3 > 1) {
+        const long yept = (sizeof(T) == 4 && g.lgP2 >= 10) ? 16 : 8;
+        const long zept = (sizeof(T) == 4 && g.lgP3 <= 5) ? 16 : 8;
+        if ((long)p.y_G * g.P2 > yept * p.y_threads) p.ok = false;
+        if (6L * p.z_KY * p.z_G * g.P3 > zept * p.z_threads) p.ok = false;
+        if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) || p.z_threads > kMaxThreads<T>)
+            p.ok = false;
+    } else if (3L * p.yc_G * g.P2 > 8L * p.yc_threads || p.yc_threads > kMaxThreadsYC<T>) {
+        p.ok = false;
+    }
     // the kx grouping divides Xp (a multiple of 16)
     const int Gmax = g.N3 > 1 ? (p.y_G > p.z_G ? p.y_G : p.z_G) : p.yc_G;
     if (g.Xp % Gmax != 0) p.ok = false;
-    if (p.x_smem > 200 * 1024 || p.y_smem > 200 * 1024 || p.z_smem > 200 * 1024 || p.yc_smem > 200 * 1024)
+    if (p.x_smem > 200 * 1024 || p.xi_smem > 200 * 1024 || p.y_smem > 200 * 1024 || p.z_smem > 200 * 1024 || p.yc_smem > 200 * 1024)
         p.ok = false;
     return p;
 }
@@ -563,7 +597,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
     } else {
         f3::lg_dispatch<1, 10>(g.lgQ, [&](auto c) {
             constexpr int LG = decltype(c)::value;
-            k_x_inv<T, CELL, LG><<<div_up(nlines, p.x_lpb), p.x_threads, p.x_smem, st>>>(g, b, out, p.x_lpb);
+            k_x_inv<T, CELL, LG><<<div_up(nlines, p.xi_lpb), p.x_threads, p.xi_smem, st>>>(g, b, out, p.xi_lpb);
         });
     }
     b.mark("demag_x_inv");

@@ -37,8 +37,10 @@ struct DemagBufs {
 // Launch shapes of the passes (lines per block bounded by the FFT engine's 16 values per thread).
 struct DemagPlan {
     bool ok;  // the grid fits the engine's per-block budget in this precision
-    int x_lpb, x_threads;
+    int x_lpb, x_threads;      // forward x pass
     size_t x_smem;
+    int xi_lpb;                // inverse x pass (same threads)
+    size_t xi_smem;
     int y_G, y_threads;
     size_t y_smem;
     int z_G, z_KY, z_threads;
