@@ -309,7 +309,7 @@ template <typename T, int LG>
 __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
 {
     if (b.ctl && b.ctl->done) return;
-    constexpr int P3 = 1 << LG;
+    constexpr int P3 = 1 << LG, H3 = P3 / 2 + 1;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
@@ -334,6 +334,18 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
             cpa_chunk((char *)(buf + z * nl + (c * R2 + r) * G) + ch * cb, (const char *)(b.S + gaddr(c, ky, z)) + ch * cb,
                       cb);
         }
+        // the tensor slice of this tile, [component][a3][row][kx], copied while the spectrum rows arrive
+        T *ten = reinterpret_cast<T *>(buf + nl * P3);
+        const int trowb = G * (int)sizeof(T);
+        const int tcb = trowb >= 16 ? 16 : trowb, tlc = __ffs(trowb / tcb) - 1, lKY = __ffs(KY) - 1;
+        for (int t = threadIdx.x; t < ((6 * H3 * KY) << tlc); t += blockDim.x) {
+            const int row = t >> tlc, ch = t - (row << tlc);
+            const int rr = row & (KY - 1), kq = row >> lKY, a3 = kq % H3, comp = kq / H3;
+            const int a2 = a20 + rr;
+            if (a2 >= g.H2) continue;
+            cpa_chunk((char *)(ten + row * G) + ch * tcb,
+                      (const char *)(b.Nk + comp * g.t_comp + ((long)a3 * g.H2 + a2) * g.Xp + kx0) + ch * tcb, tcb);
+        }
         cpa_wait_all();
         __syncthreads();
     }
@@ -342,16 +354,28 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
                                                     f3::NoFn<T>());
     const int npts = KY * G * P3;
     const int lG = __ffs(G) - 1, lKY = __ffs(KY) - 1;
+    const T *ten = reinterpret_cast<const T *>(buf + nl * P3);
+    const int tstride = H3 * KY * G;
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
         const int gg = t & (G - 1), q = t >> lG, rr = q & (KY - 1), kz = q >> lKY;
         const int a2 = a20 + rr;
         if (a2 >= g.H2) continue;
-        const Ten6<T> ten = tensor_at(g, b, kx0 + gg, a2, kz);
+        const int a3 = kz <= (P3 >> 1) ? kz : P3 - kz;
+        const T s3 = kz <= (P3 >> 1) ? T(1) : T(-1);
+        const T *tp = ten + (a3 * KY + rr) * G + gg;
+        Ten6<T> tt;
+        tt.xx = tp[0];
+        tt.yy = tp[tstride];
+        tt.zz = tp[2 * tstride];
+        tt.xy = tp[3 * tstride];
+        tt.xz = tp[4 * tstride] * s3;
+        tt.yz = tp[5 * tstride] * s3;
+        const Ten6<T> &ten6 = tt;
         Cx<T> *p = buf + kz * nl + rr * G + gg;
-        tensor_mul(ten, T(1), p, p + R2 * G, p + 2 * R2 * G);
+        tensor_mul(ten6, T(1), p, p + R2 * G, p + 2 * R2 * G);
         if (a2 > 0 && a2 < h2) {
             Cx<T> *pm = p + KY * G;
-            tensor_mul(ten, T(-1), pm, pm + R2 * G, pm + 2 * R2 * G);
+            tensor_mul(ten6, T(-1), pm, pm + R2 * G, pm + 2 * R2 * G);
         }
     }
     __syncthreads();
@@ -517,7 +541,7 @@ DemagPlan demag_plan(const Geom &g)
         p.z_G = Gz;
         p.z_KY = KY;
         p.z_threads = threads_for(6L * KY * Gz * g.P3 * 8 / zept);
-        p.z_smem = (size_t)6 * KY * Gz * g.P3 * cs;
+        p.z_smem = (size_t)6 * KY * Gz * g.P3 * cs + (size_t)6 * (g.P3 / 2 + 1) * KY * Gz * sizeof(T);
     } else {
         int G = pow2_floor(8L * kMaxThreadsYC<T> / (3L * g.P2));
         G = G > 16 ? 16 : G;
