@@ -107,10 +107,13 @@ struct NodeField {
     bool magnetic;
 };
 
-// Effective field at node (n1, n2, n3) = (x0 + tx, y0 + ty, z) from the shared planes.  INTERIOR:
-// every cell around the node exists and the material is uniform, so the 27 assembled weights are
-// constants.
-template <typename T, bool INTERIOR>
+// Effective field at node (n1, n2, n3) = (x0 + tx, y0 + ty, z) from the shared planes.
+//   MODE 1 (interior, uniform material): every cell around the node exists, the 27 assembled weights
+//          are constants;
+//   MODE 2 (uniform material, any node): the weight of an offset is the per-pattern constant times the
+//          number of mesh cells holding both nodes, the product of per-axis counts;
+//   MODE 0 (general): the weights are summed over the adjacent cells' material values.
+template <typename T, int MODE>
 __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const NodeSmem<T> &sm, int n1, int n2,
                                                    int n3, int n, int tx, int ty)
 {
@@ -128,7 +131,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
     const T im = p.inv_mass[n];
     f.magnetic = im > T(0);
     T ex = 0, ey = 0, ez = 0, pe = 0;
-    if (INTERIOR) {
+    if (MODE == 1) {
         // sum_o w_o (m_{n+o} - m_n) = sum_{o != 0} w_o m_{n+o} - (sum w) m_n;  anisotropy: sum_o c_o m_{n+o}
         T sx = 0, sy = 0, sz = 0, ax = 0, ay = 0, az = 0;
 #pragma unroll
@@ -153,6 +156,43 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
         ex = sx - p.wex_sum * f.mx;
         ey = sy - p.wex_sum * f.my;
         ez = sz - p.wex_sum * f.mz;
+        pe = p.e0 * ax + p.e1 * ay + p.e2 * az;
+    } else if (MODE == 2) {
+        // cells n_k - 1 (pattern i_k = 1) and n_k (i_k = 0) along each axis
+        const int cm1 = n1 >= 1 && n1 - 1 < g.N1, cp1 = n1 < g.N1;
+        const int cm2 = n2 >= 1 && n2 - 1 < g.N2, cp2 = n2 < g.N2;
+        const int cm3 = n3 >= 1 && n3 - 1 < g.N3, cp3 = n3 < g.N3;
+        T sx = 0, sy = 0, sz = 0, ax = 0, ay = 0, az = 0, wsum = 0;
+#pragma unroll
+        for (int o3 = -1; o3 <= 1; ++o3) {
+            const int slot = o3 < 0 ? szm : (o3 > 0 ? szp : sz0);
+            const int k3 = o3 < 0 ? cm3 : (o3 > 0 ? cp3 : cm3 + cp3);
+#pragma unroll
+            for (int o2 = -1; o2 <= 1; ++o2) {
+                const int k23 = k3 * (o2 < 0 ? cm2 : (o2 > 0 ? cp2 : cm2 + cp2));
+#pragma unroll
+                for (int o1 = -1; o1 <= 1; ++o1) {
+                    const int cnt = k23 * (o1 < 0 ? cm1 : (o1 > 0 ? cp1 : cm1 + cp1));
+                    const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
+                    const T fc = (T)cnt;
+                    const V4<T> q = sm.y[slot][cy0 + o2][cx0 + o1];
+                    if (d != 0) {
+                        const T w = p.wexd[d] * fc;
+                        sx += w * q.x;
+                        sy += w * q.y;
+                        sz += w * q.z;
+                        wsum += w;
+                    }
+                    const T wa = p.wand[d] * fc;
+                    ax += wa * q.x;
+                    ay += wa * q.y;
+                    az += wa * q.z;
+                }
+            }
+        }
+        ex = sx - wsum * f.mx;
+        ey = sy - wsum * f.my;
+        ez = sz - wsum * f.mz;
         pe = p.e0 * ax + p.e1 * ay + p.e2 * az;
     } else {
         T a[8], ku[8];
@@ -301,8 +341,9 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
         const bool interior = tile_inner && z >= 1 && z <= g.N3 - 1;
         if (active) {
             const int n = (z * g.nn2 + n2) * g.nn1 + n1;
-            const NodeField<T> f = interior ? node_field<T, true>(p, sm, n1, n2, z, n, tx, ty)
-                                            : node_field<T, false>(p, sm, n1, n2, z, n, tx, ty);
+            const NodeField<T> f = interior    ? node_field<T, 1>(p, sm, n1, n2, z, n, tx, ty)
+                                   : p.uniform ? node_field<T, 2>(p, sm, n1, n2, z, n, tx, ty)
+                                               : node_field<T, 0>(p, sm, n1, n2, z, n, tx, ty);
             if (!STAGE) {
                 out[n] = f.hx;
                 out[ns + n] = f.hy;

@@ -17,6 +17,9 @@ struct LocalParams {
     // anisotropy, and the sum of the exchange weights.  uniform = 0 disables that path.
     int uniform;
     T wex27[27], wan27[27], wex_sum;
+    // uniform material at any node: Wex[d] A and Wm[d] Ku (0 for terms that are off); the weight of an
+    // offset is this times the number of mesh cells that hold both nodes, a product of per-axis counts
+    T wexd[8], wand[8];
     T mu0V8;           // mu0 * V / 8
     const T *A;        // cell maps (n_cells) or NULL for the uniform value
     const T *Ku;

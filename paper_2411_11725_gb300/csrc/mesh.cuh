@@ -214,6 +214,10 @@ inline LocalParams<T> local_params(nm_mesh M, unsigned terms)
                     wsum += we;
                 }
         p.wex_sum = (T)wsum;
+        for (int d = 0; d < 8; ++d) {
+            p.wexd[d] = (T)((double)p.Wex[d] * A);
+            p.wand[d] = (T)((double)p.Wm[d] * Ku);
+        }
     }
     p.gam = M->gamma / (1.0 + M->alpha * M->alpha);
     p.alpha = M->alpha;
