@@ -197,6 +197,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 3 : 2)
         const Cx<T> Xc = conj(Xq);
         return (Xk + Xc) + mul_si((Xk - Xc) * conj(tw[k << wsh]), 1);
     };
+#pragma unroll 4
     for (int t = threadIdx.x; t < nl * H; t += blockDim.x) {
         const int l = t >> (LG - 1 < 0 ? 0 : LG - 1), k = t & (H - 1);
         const Cx<T> *s = b.S + info[l].spec;
