@@ -61,6 +61,43 @@ __host__ __device__ constexpr int bitrev(int i)
     return r;
 }
 
+// FP32 complex sum and difference as packed pairs (add.rn.f32x2 / sub.rn.f32x2: one instruction for
+// both parts, rounded exactly as the scalar additions)
+__device__ __forceinline__ unsigned long long pack2(Cx<float> a)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+    return r;
+}
+__device__ __forceinline__ Cx<float> unpack2(unsigned long long r)
+{
+    Cx<float> a;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+    return a;
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> csum(Cx<T> a, Cx<T> b)
+{
+    if constexpr (sizeof(T) == 4) {
+        unsigned long long d;
+        asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+        return unpack2(d);
+    } else {
+        return a + b;
+    }
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> cdiff(Cx<T> a, Cx<T> b)
+{
+    if constexpr (sizeof(T) == 4) {
+        unsigned long long d;
+        asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(pack2(a)), "l"(pack2(b)));
+        return unpack2(d);
+    } else {
+        return a - b;
+    }
+}
+
 // x_k <- sum_j x_j e^{DIR 2 pi i jk / R}: radix-2 decimation-in-frequency network, X_k in x[bitrev(k)]
 template <typename T, int R, int DIR>
 __device__ __forceinline__ void dft(Cx<T> *x)
@@ -72,8 +109,8 @@ __device__ __forceinline__ void dft(Cx<T> *x)
 #pragma unroll
             for (int k = 0; k < h; ++k) {
                 const Cx<T> a = x[s + k], b = x[s + k + h];
-                x[s + k] = a + b;
-                const Cx<T> d = a - b;
+                x[s + k] = csum(a, b);
+                const Cx<T> d = cdiff(a, b);
                 const int q = k * (8 / h);  // W_{2h}^k = W_16^q
                 if (q == 0) x[s + k + h] = d;
                 else if (q == 4) x[s + k + h] = mul_si(d, DIR);
