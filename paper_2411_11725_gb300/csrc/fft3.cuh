@@ -51,6 +51,11 @@ __host__ __device__ constexpr double c16(int k)
     }
 }
 __host__ __device__ constexpr double s16(int k) { return c16(k - 4); }
+// the same cosines as a table of the working precision (indexed with unrolled constants)
+template <typename T>
+__device__ constexpr T kC16[16] = {(T)c16(0),  (T)c16(1),  (T)c16(2),  (T)c16(3), (T)c16(4),  (T)c16(5),
+                                   (T)c16(6),  (T)c16(7),  (T)c16(8),  (T)c16(9), (T)c16(10), (T)c16(11),
+                                   (T)c16(12), (T)c16(13), (T)c16(14), (T)c16(15)};
 
 template <int R>
 __host__ __device__ constexpr int bitrev(int i)
@@ -115,7 +120,7 @@ __device__ __forceinline__ void dft(Cx<T> *x)
                 if (q == 0) x[s + k + h] = d;
                 else if (q == 4) x[s + k + h] = mul_si(d, DIR);
                 else {
-                    const T cq = (T)c16(q), sq = (T)(DIR > 0 ? s16(q) : -s16(q));
+                    const T cq = kC16<T>[q & 15], sq = DIR > 0 ? kC16<T>[(q - 4) & 15] : -kC16<T>[(q - 4) & 15];
                     x[s + k + h] = cx<T>(d.x * cq - d.y * sq, d.x * sq + d.y * cq);
                 }
             }

@@ -326,6 +326,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
     const int ns = (int)g.ns;
     double dt = 0.0;
     if (STAGE) dt = sa.ctl ? sa.ctl->dt : 0.0;
+    const float dtf = (float)dt;
     // the tile's x-y footprint has all eight cells around every node (uniform material)
     const bool tile_inner = p.uniform && x0 >= 1 && x0 + kTX <= g.N1 && y0 >= 1 && y0 + TY <= g.N2;
     for (int z = z0; z < z1; ++z) {
@@ -358,7 +359,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
                     const T bx = f.my * az - f.mz * ay;
                     const T by = f.mz * ax - f.mx * az;
                     const T bz = f.mx * ay - f.my * ax;
-                    const T gm = (T)p.gam, al = (T)p.alpha;
+                    const T gm = p.gam_t, al = p.alpha_t;
                     kx = -gm * (ax + al * bx);
                     ky = -gm * (ay + al * by);
                     kz = -gm * (az + al * bz);
@@ -386,7 +387,6 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
                     az += as * kz;
                     if (sizeof(T) == 4 && sa.mf) {
                         // FP32 path: y_{s+1} is an FP32 quantity, formed from the FP32 copy of m
-                        const float dtf = (float)dt;
                         y_next[n] = (T)(sa.mf[n] + dtf * (float)ax);
                         y_next[ns + n] = (T)(sa.mf[ns + n] + dtf * (float)ay);
                         y_next[2 * ns + n] = (T)(sa.mf[2 * ns + n] + dtf * (float)az);

@@ -32,6 +32,7 @@ struct LocalParams {
     double hu0, hu1, hu2, hu_freq, hu_phase, hc_freq, hc_phase;
     unsigned terms;
     double gam;        // gamma / (1 + alpha^2)
+    T gam_t, alpha_t;  // the same in the working precision
     int raw;           // 1: output -dE (no division by the mass, no uniform applied field)
     double alpha;
 };

@@ -221,6 +221,8 @@ inline LocalParams<T> local_params(nm_mesh M, unsigned terms)
     }
     p.gam = M->gamma / (1.0 + M->alpha * M->alpha);
     p.alpha = M->alpha;
+    p.gam_t = (T)p.gam;
+    p.alpha_t = (T)p.alpha;
     return p;
 }
 
