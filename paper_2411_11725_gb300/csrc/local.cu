@@ -115,7 +115,7 @@ struct NodeField {
 //   MODE 0 (general): the weights are summed over the adjacent cells' material values.
 template <typename T, int MODE>
 __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, const NodeSmem<T> &sm, int n1, int n2,
-                                                   int n3, int n, int tx, int ty)
+                                                   int n3, T im, int tx, int ty)
 {
     const Geom &g = p.g;
     const int sz0 = (n3 + kNodeSlots) % kNodeSlots, szm = (n3 + kNodeSlots - 1) % kNodeSlots,
@@ -128,7 +128,6 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
         f.my = m.y;
         f.mz = m.z;
     }
-    const T im = p.inv_mass[n];
     f.magnetic = im > T(0);
     T ex = 0, ey = 0, ez = 0, pe = 0;
     if (MODE == 1) {
@@ -337,14 +336,38 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
             load_cell_plane(p, sm, z + 1, x0, y0);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
+        // this node's own values (1/mass; for the next stage input, the earlier slopes and the FP32 copy
+        // of m) do not depend on the shared planes: their loads are issued before the wait and barrier
+        const int n = (z * g.nn2 + n2) * g.nn1 + n1;
+        T im = T(0), px = 0, py = 0, pz = 0;
+        float mfx = 0.f, mfy = 0.f, mfz = 0.f;
+        if (active) {
+            im = p.inv_mass[n];
+            if (STAGE && y_next) {
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    if (j + 1 >= sa.s) break;
+                    const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
+                    if (aj == T(0)) continue;
+                    const T *kj = (const T *)sa.k[j];
+                    px += aj * kj[n];
+                    py += aj * kj[ns + n];
+                    pz += aj * kj[2 * ns + n];
+                }
+                if (sizeof(T) == 4 && sa.mf) {
+                    mfx = sa.mf[n];
+                    mfy = sa.mf[ns + n];
+                    mfz = sa.mf[2 * ns + n];
+                }
+            }
+        }
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
         const bool interior = tile_inner && z >= 1 && z <= g.N3 - 1;
         if (active) {
-            const int n = (z * g.nn2 + n2) * g.nn1 + n1;
-            const NodeField<T> f = interior    ? node_field<T, 1>(p, sm, n1, n2, z, n, tx, ty)
-                                   : p.uniform ? node_field<T, 2>(p, sm, n1, n2, z, n, tx, ty)
-                                               : node_field<T, 0>(p, sm, n1, n2, z, n, tx, ty);
+            const NodeField<T> f = interior    ? node_field<T, 1>(p, sm, n1, n2, z, im, tx, ty)
+                                   : p.uniform ? node_field<T, 2>(p, sm, n1, n2, z, im, tx, ty)
+                                               : node_field<T, 0>(p, sm, n1, n2, z, im, tx, ty);
             if (!STAGE) {
                 out[n] = f.hx;
                 out[ns + n] = f.hy;
@@ -370,26 +393,13 @@ __global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const
                 if (y_next) {
                     // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working
                     // precision
-                    T ax = 0, ay = 0, az = 0;
-#pragma unroll
-                    for (int j = 0; j < 7; ++j) {
-                        if (j + 1 >= sa.s) break;
-                        const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
-                        if (aj == T(0)) continue;
-                        const T *kj = (const T *)sa.k[j];
-                        ax += aj * kj[n];
-                        ay += aj * kj[ns + n];
-                        az += aj * kj[2 * ns + n];
-                    }
                     const T as = sizeof(T) == 4 ? (T)sa.af[sa.s - 1] : (T)sa.a[sa.s - 1];
-                    ax += as * kx;
-                    ay += as * ky;
-                    az += as * kz;
+                    const T ax = px + as * kx, ay = py + as * ky, az = pz + as * kz;
                     if (sizeof(T) == 4 && sa.mf) {
                         // FP32 path: y_{s+1} is an FP32 quantity, formed from the FP32 copy of m
-                        y_next[n] = (T)(sa.mf[n] + dtf * (float)ax);
-                        y_next[ns + n] = (T)(sa.mf[ns + n] + dtf * (float)ay);
-                        y_next[2 * ns + n] = (T)(sa.mf[2 * ns + n] + dtf * (float)az);
+                        y_next[n] = (T)(mfx + dtf * (float)ax);
+                        y_next[ns + n] = (T)(mfy + dtf * (float)ay);
+                        y_next[2 * ns + n] = (T)(mfz + dtf * (float)az);
                     } else {
                         y_next[n] = (T)(sa.m[n] + dt * (double)ax);
                         y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)ay);
