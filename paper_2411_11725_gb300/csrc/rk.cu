@@ -90,7 +90,7 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, 
                 const float m0 = mf ? mf[i] : (float)m[i], dtf = (float)dt;
                 const float m5 = m0 + dtf * (float)sb;
                 const float sc = (float)atol + (float)rtol * fmaxf(fabsf(m0), fabsf(m5));
-                const float q = dtf * (float)se / sc;
+                const float q = __fdividef(dtf * (float)se, sc);  // a weight of the norm: fast division
                 part += (T)(q * q);
             }
         }
