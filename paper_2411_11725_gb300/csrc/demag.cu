@@ -24,10 +24,29 @@ constexpr int kMinBlocks = (sizeof(T) == 4 && LG < 11) ? 2 : 1;
 // values per thread per FFT stage in the y passes: radix-16 stages for the long FP32 lines
 template <typename T, int LG>
 constexpr int kYEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
-// z pass: 16 values per thread for short FP32 lines (up to 32), so that a block spans 16 kx columns
-// (128-byte rows); longer lines keep 8 (measured faster)
+constexpr int pow2_floor_c(int v)
+{
+    int p = 1;
+    while (2 * p <= v) p *= 2;
+    return p;
+}
+// Compile-time tile of the z convolution for lines of 2^LG: G kx columns x KY octant rows (each with its
+// mirror) x 3 components, 16 values per thread for short FP32 lines (128-byte rows), 8 otherwise.
 template <typename T, int LG>
-constexpr int kZEpt = (sizeof(T) == 4 && LG <= 5) ? 16 : 8;
+struct ZTile {
+    static constexpr int P3 = 1 << LG;
+    static constexpr int EPT = (sizeof(T) == 4 && LG <= 5) ? 16 : 8;
+    static constexpr int BUDGET = EPT * kMaxThreads<T>;
+    static constexpr int G0 = EPT == 16 ? 16 : (int)(64 / sizeof(Cx<T>));
+    static constexpr int fit_g(int g) { return (g > 1 && 6 * g * P3 > BUDGET) ? fit_g(g / 2) : g; }
+    static constexpr int G = fit_g(G0);
+    static constexpr int KY = pow2_floor_c(BUDGET / (6 * G * P3)) > 0 ? pow2_floor_c(BUDGET / (6 * G * P3)) : 1;
+    static constexpr int NL = 6 * KY * G;
+    static constexpr int THREADS = ((NL * P3 / EPT > 32 ? NL * P3 / EPT : 32) + 31) / 32 * 32;
+    static constexpr size_t SMEM = (size_t)NL * P3 * sizeof(Cx<T>) + (size_t)6 * (P3 / 2 + 1) * KY * G * sizeof(T);
+    static_assert(NL * P3 <= EPT * THREADS && THREADS <= kMaxThreads<T>, "z tile exceeds the block");
+};
+
 // forward x pass: radix-16 stages for FP32 lines of 2^10 complex values (the inverse keeps 8: measured)
 template <typename T, int LG>
 constexpr int kXEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
@@ -307,14 +326,15 @@ __device__ __forceinline__ void tensor_mul(const Ten6<T> &t, T s2, Cx<T> *px, Cx
 // Rows r < KY are ky = a2_0 + r, rows KY + r are ky = P2 - (a2_0 + r) (present when 0 < a2 < P2/2).
 // Lines l = (c * 2KY + r) * G + g; element kz of line l at buf[kz * nl + l].
 template <typename T, int LG>
-__global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g, DemagBufs<T> b, int G, int KY)
+__global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g, DemagBufs<T> b)
 {
     if (b.ctl && b.ctl->done) return;
-    constexpr int P3 = 1 << LG, H3 = P3 / 2 + 1;
+    using Z = ZTile<T, LG>;
+    constexpr int P3 = 1 << LG, H3 = P3 / 2 + 1, G = Z::G, KY = Z::KY;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
-    const int R2 = 2 * KY, nl = 3 * R2 * G;
+    constexpr int R2 = 2 * KY, nl = 3 * R2 * G;
     const int h2 = g.P2 >> 1;
     auto row_ky = [&](int r) -> int {  // -1: row absent
         const int a2 = a20 + (r < KY ? r : r - KY);
@@ -324,12 +344,12 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
     };
     auto gaddr = [&](int c, int ky, int z) -> long { return c * g.s_comp + ((long)z * g.P2 + ky) * g.Xp + kx0; };
     {
-        const int rowb = G * (int)sizeof(Cx<T>);
-        const int cb = rowb >= 16 ? 16 : rowb, lcpr = __ffs(rowb / cb) - 1, lR2 = __ffs(R2) - 1;
+        constexpr int rowb = G * (int)sizeof(Cx<T>);
+        constexpr int cb = rowb >= 16 ? 16 : rowb, lcpr = rowb / cb == 1 ? 0 : (rowb / cb == 2 ? 1 : (rowb / cb == 4 ? 2 : 3));
         const int nrow = g.N3 * 3 * R2;
         for (int t = threadIdx.x; t < (nrow << lcpr); t += blockDim.x) {
             const int rr = t >> lcpr, ch = t - (rr << lcpr);
-            const int r = rr & (R2 - 1), cz = rr >> lR2, z = cz / 3, c = cz - 3 * z;
+            const int r = rr % R2, cz = rr / R2, z = cz / 3, c = cz - 3 * z;
             const int ky = row_ky(r);
             if (ky < 0) continue;
             cpa_chunk((char *)(buf + z * nl + (c * R2 + r) * G) + ch * cb, (const char *)(b.S + gaddr(c, ky, z)) + ch * cb,
@@ -337,11 +357,11 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
         }
         // the tensor slice of this tile, [component][a3][row][kx], copied while the spectrum rows arrive
         T *ten = reinterpret_cast<T *>(buf + nl * P3);
-        const int trowb = G * (int)sizeof(T);
-        const int tcb = trowb >= 16 ? 16 : trowb, tlc = __ffs(trowb / tcb) - 1, lKY = __ffs(KY) - 1;
-        for (int t = threadIdx.x; t < ((6 * H3 * KY) << tlc); t += blockDim.x) {
-            const int row = t >> tlc, ch = t - (row << tlc);
-            const int rr = row & (KY - 1), kq = row >> lKY, a3 = kq % H3, comp = kq / H3;
+        constexpr int trowb = G * (int)sizeof(T);
+        constexpr int tcb = trowb >= 16 ? 16 : trowb, tch = trowb / tcb;
+        for (int t = threadIdx.x; t < 6 * H3 * KY * tch; t += blockDim.x) {
+            const int row = t / tch, ch = t - row * tch;
+            const int rr = row % KY, kq = row / KY, a3 = kq % H3, comp = kq / H3;
             const int a2 = a20 + rr;
             if (a2 >= g.H2) continue;
             cpa_chunk((char *)(ten + row * G) + ch * tcb,
@@ -350,15 +370,14 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
         cpa_wait_all();
         __syncthreads();
     }
-    const FastDiv nlf((unsigned)nl);
-    f3::fft<T, LG, -1, true, true, true, kZEpt<T, LG>>(buf, nl, nlf, b.tw, g.twlg, g.N3, P3, f3::NoFn<T>(),
+    const FastDiv nlf(1u);  // unused: the line count is a compile-time constant
+    f3::fft<T, LG, -1, true, true, true, Z::EPT, nl>(buf, nl, nlf, b.tw, g.twlg, g.N3, P3, f3::NoFn<T>(),
                                                     f3::NoFn<T>());
-    const int npts = KY * G * P3;
-    const int lG = __ffs(G) - 1, lKY = __ffs(KY) - 1;
+    constexpr int npts = KY * G * P3;
     const T *ten = reinterpret_cast<const T *>(buf + nl * P3);
-    const int tstride = H3 * KY * G;
+    constexpr int tstride = H3 * KY * G;
     for (int t = threadIdx.x; t < npts; t += blockDim.x) {
-        const int gg = t & (G - 1), q = t >> lG, rr = q & (KY - 1), kz = q >> lKY;
+        const int gg = t % G, q = t / G, rr = q % KY, kz = q / KY;
         const int a2 = a20 + rr;
         if (a2 >= g.H2) continue;
         const int a3 = kz <= (P3 >> 1) ? kz : P3 - kz;
@@ -381,11 +400,11 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
     }
     __syncthreads();
     auto dst = [&](int l, int z, Cx<T> v) {
-        const int gg = l & (G - 1), q = l >> lG, r = q & (R2 - 1), c = q >> (lKY + 1);
+        const int gg = l % G, q = l / G, r = q % R2, c = q / R2;
         const int ky = row_ky(r);
         if (ky >= 0) b.S[gaddr(c, ky, z) + gg] = v;
     };
-    f3::fft<T, LG, +1, true, true, false, kZEpt<T, LG>>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
+    f3::fft<T, LG, +1, true, true, false, Z::EPT, nl>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
 }
 
 // Single-layer variant (N3 == 1, P3 == 1): forward y, tensor product at kz = 0 (each octant row a2
@@ -530,19 +549,14 @@ DemagPlan demag_plan(const Geom &g)
         p.y_G = G < 1 ? 1 : G;
         p.y_threads = threads_for((long)p.y_G * g.P2 * 8 / yept);
         p.y_smem = (size_t)p.y_G * g.P2 * cs;
-        const int zept = (sizeof(T) == 4 && g.lgP3 <= 5) ? 16 : 8;
-        const long zbudget = (long)zept * kMaxThreads<T>;
-        int Gz = zept == 16 ? 16 : Gmin, KY = 0;
-        while (Gz >= 1 && (KY = pow2_floor(zbudget / (6L * Gz * g.P3))) < 1) Gz /= 2;
-        if (Gz < 1 || KY < 1 || g.lgP3 > 7) p.ok = false;
-        Gz = Gz < 1 ? 1 : Gz;
-        KY = KY < 1 ? 1 : KY;
-        const int kyc = pow2_floor(g.H2);
-        KY = KY > kyc ? kyc : KY;
-        p.z_G = Gz;
-        p.z_KY = KY;
-        p.z_threads = threads_for(6L * KY * Gz * g.P3 * 8 / zept);
-        p.z_smem = (size_t)6 * KY * Gz * g.P3 * cs + (size_t)6 * (g.P3 / 2 + 1) * KY * Gz * sizeof(T);
+        if (g.lgP3 < 1 || g.lgP3 > 7) p.ok = false;
+        f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
+            using Z = ZTile<T, decltype(c)::value>;
+            p.z_G = Z::G;
+            p.z_KY = Z::KY;
+            p.z_threads = Z::THREADS;
+            p.z_smem = Z::SMEM;
+        });
     } else {
         int G = pow2_floor(8L * kMaxThreadsYC<T> / (3L * g.P2));
         G = G > 16 ? 16 : G;
@@ -558,9 +572,7 @@ DemagPlan demag_plan(const Geom &g)
     }
     if (g.N3 > 1) {
         const long yept = (sizeof(T) == 4 && g.lgP2 >= 10) ? 16 : 8;
-        const long zept = (sizeof(T) == 4 && g.lgP3 <= 5) ? 16 : 8;
         if ((long)p.y_G * g.P2 > yept * p.y_threads) p.ok = false;
-        if (6L * p.z_KY * p.z_G * g.P3 > zept * p.z_threads) p.ok = false;
         if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) || p.z_threads > kMaxThreads<T>)
             p.ok = false;
     } else if (3L * p.yc_G * g.P2 > 8L * p.yc_threads || p.yc_threads > kMaxThreadsYC<T>) {
@@ -599,8 +611,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         }
         f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
             constexpr int LG = decltype(c)::value;
-            k_z_conv<T, LG><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b, p.z_G,
-                                                                                                    p.z_KY);
+            k_z_conv<T, LG><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b);
         });
         b.mark("demag_z_conv");
         if (g.P2 > 1) {

@@ -142,11 +142,12 @@ enum { OUT_FN = 0, OUT_SM = 1 };
 
 // One stage S of a length-2^LG transform on nl lines (nb = nl * 2^LG / R butterflies).
 template <typename T, int LG, int S, int DIR, bool LF, int IN, int OUT, bool SYNC_IN, bool SYNC_OUT, int EPT,
-          typename Src, typename Dst>
-__device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl, const FastDiv &nlf,
+          int NLC, typename Src, typename Dst>
+__device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const FastDiv &nlf,
                                       const Cx<T> *__restrict__ tw, int twlg, int nin, int nout, const Src &src,
                                       const Dst &dst)
 {
+    const int nl = NLC > 0 ? NLC : nl_rt;  // a compile-time line count turns the index arithmetic into constants
     constexpr int RM = EPT == 16 ? 4 : 3;
     constexpr int RLG = stage_lg(LG, S, RM), R = 1 << RLG, SLG = stage_slg(LG, S, RM), NS = 1 << SLG;
     constexpr int L = 1 << LG, LR = L >> RLG, LSZ = padded(L), BPT = EPT / R;
@@ -158,7 +159,7 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl, const Fas
         const int b = threadIdx.x + c * blockDim.x;
         int j, l;
         if (LF) {
-            j = (int)nlf.div((unsigned)b);
+            j = NLC > 0 ? b / NLC : (int)nlf.div((unsigned)b);
             l = b - j * nl;
         } else {
             j = b & (LR - 1);
@@ -232,7 +233,8 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl, const Fas
     if (SYNC_OUT) __syncthreads();
 }
 
-template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT, typename Src, typename Dst>
+template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT, int NLC, typename Src,
+          typename Dst>
 __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw,
                                            int twlg, int nin, int nout, const Src &src, const Dst &dst)
 {
@@ -243,9 +245,9 @@ __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nl
         constexpr int OUT = (last && !DST_SM) ? OUT_FN : OUT_SM;
         constexpr bool SYNC_IN = IN == IN_SM && OUT == OUT_SM;  // in place: all reads before any write
         constexpr bool SYNC_OUT = OUT == OUT_SM;
-        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT, EPT>(buf, nl, nlf, tw, twlg, first ? nin : (1 << LG),
-                                                               last ? nout : (1 << LG), src, dst);
-        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM, EPT>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT, EPT, NLC>(buf, nl, nlf, tw, twlg, first ? nin : (1 << LG),
+                                                                    last ? nout : (1 << LG), src, dst);
+        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM, EPT, NLC>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
     }
 }
 
@@ -253,14 +255,16 @@ __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nl
 // SRC_SM: the first stage reads the shared layout (the caller synchronised after filling it);
 // otherwise src(l, i) is called for i < nin.  DST_SM: the last stage writes the shared layout
 // (followed by a barrier); otherwise dst(l, o, v) is called for o < nout.
-// EPT (8 or 16) values per thread per stage: needs nl * 2^LG <= EPT * blockDim.x.
-template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT = 8, typename Src, typename Dst>
+// EPT (8 or 16) values per thread per stage: needs nl * 2^LG <= EPT * blockDim.x.  NLC > 0: the line
+// count is the compile-time constant NLC (nl and nlf are then ignored).
+template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT = 8, int NLC = 0, typename Src,
+          typename Dst>
 __device__ __forceinline__ void fft(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw, int twlg,
                                     int nin, int nout, const Src &src, const Dst &dst)
 {
     static_assert(LG >= 1, "length-1 transforms are copies");
     static_assert(EPT == 8 || EPT == 16, "8 or 16 values per thread");
-    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM, EPT>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM, EPT, NLC>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
 }
 
 // placeholder functor for a stage side that is shared memory
