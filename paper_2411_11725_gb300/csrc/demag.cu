@@ -47,6 +47,19 @@ struct ZTile {
     static_assert(NL * P3 <= EPT * THREADS && THREADS <= kMaxThreads<T>, "z tile exceeds the block");
 };
 
+// Compile-time tile of the y passes for lines of 2^LG: G kx columns, EPT values per thread.
+template <typename T, int LG>
+struct YTile {
+    static constexpr int P2 = 1 << LG;
+    static constexpr int EPT = kYEpt<T, LG>;
+    static constexpr int MAXT = kMaxThreads<T, LG>;
+    static constexpr int G0 = pow2_floor_c(EPT * MAXT / P2);
+    static constexpr int G = G0 > 16 ? 16 : (G0 < 1 ? 1 : G0);
+    static constexpr int THREADS = ((G * P2 / EPT > 32 ? G * P2 / EPT : 32) + 31) / 32 * 32;
+    static constexpr size_t SMEM = (size_t)G * P2 * sizeof(Cx<T>);
+    static_assert(G * P2 <= EPT * THREADS && THREADS <= MAXT, "y tile exceeds the block");
+};
+
 // forward x pass: radix-16 stages for FP32 lines of 2^10 complex values (the inverse keeps 8: measured)
 template <typename T, int LG>
 constexpr int kXEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
@@ -268,27 +281,27 @@ __global__ void k_x_inv1(Geom g, DemagBufs<T> b, T *__restrict__ out)
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
 // Shared layout: row y at buf + y * G (lines = columns, fastest).
 template <typename T, int LG, int DIR>
-__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geom g, DemagBufs<T> b, int G)
+__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geom g, DemagBufs<T> b)
 {
     if (b.ctl && b.ctl->done) return;
-    constexpr int P2 = 1 << LG;
+    constexpr int P2 = 1 << LG, G = YTile<T, LG>::G;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
     const int nin = DIR < 0 ? g.N2 : P2, nout = DIR < 0 ? P2 : g.N2;
     const int Xp = g.Xp;
-    const int rowb = G * (int)sizeof(Cx<T>);
-    const int cb = rowb >= 16 ? 16 : rowb;
-    const int lcpr = __ffs(rowb / cb) - 1;  // copies per row is a power of two
-    for (int t = threadIdx.x; t < (nin << lcpr); t += blockDim.x) {
-        const int y = t >> lcpr, ch = t - (y << lcpr);
+    constexpr int rowb = G * (int)sizeof(Cx<T>);
+    constexpr int cb = rowb >= 16 ? 16 : rowb;
+    constexpr int cpr = rowb / cb;  // copies per row
+    for (int t = threadIdx.x; t < nin * cpr; t += blockDim.x) {
+        const int y = t / cpr, ch = t - y * cpr;
         cpa_chunk((char *)(buf + y * G) + ch * cb, (const char *)(base + y * Xp) + ch * cb, cb);
     }
     cpa_wait_all();
     __syncthreads();
     auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    f3::fft<T, LG, DIR, true, true, false, kYEpt<T, LG>>(buf, G, FastDiv((unsigned)G), b.tw, g.twlg, nin, nout,
-                                                         f3::NoFn<T>(), dst);
+    f3::fft<T, LG, DIR, true, true, false, kYEpt<T, LG>, G>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, nout,
+                                                            f3::NoFn<T>(), dst);
 }
 
 // The six real tensor components at octant frequency (kx, a2, kz), with the sign of the odd ones in
@@ -541,14 +554,15 @@ DemagPlan demag_plan(const Geom &g)
         p.x_smem = 0;
     }
     if (g.N3 > 1) {
-        const int yept = (sizeof(T) == 4 && g.lgP2 >= 10) ? 16 : 8;
-        const long ybudget = (long)yept * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 1024 : 512);
-        int G = pow2_floor(ybudget / g.P2);
-        G = G > 16 ? 16 : G;
-        if (G < 1 || g.lgP2 > 11) p.ok = false;
-        p.y_G = G < 1 ? 1 : G;
-        p.y_threads = threads_for((long)p.y_G * g.P2 * 8 / yept);
-        p.y_smem = (size_t)p.y_G * g.P2 * cs;
+        // (P2 == 1: no y passes)
+        p.y_G = 1;
+        if (g.lgP2 > 11) p.ok = false;
+        f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
+            using Y = YTile<T, decltype(c)::value>;
+            p.y_G = Y::G;
+            p.y_threads = Y::THREADS;
+            p.y_smem = Y::SMEM;
+        });
         if (g.lgP3 < 1 || g.lgP3 > 7) p.ok = false;
         f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
             using Z = ZTile<T, decltype(c)::value>;
@@ -571,8 +585,6 @@ DemagPlan demag_plan(const Geom &g)
         if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > 8L * p.x_threads) p.ok = false;
     }
     if (g.N3 > 1) {
-        const long yept = (sizeof(T) == 4 && g.lgP2 >= 10) ? 16 : 8;
-        if ((long)p.y_G * g.P2 > yept * p.y_threads) p.ok = false;
         if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) || p.z_threads > kMaxThreads<T>)
             p.ok = false;
     } else if (3L * p.yc_G * g.P2 > 8L * p.yc_threads || p.yc_threads > kMaxThreadsYC<T>) {
@@ -605,7 +617,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
                 constexpr int LG = decltype(c)::value;
-                k_y<T, LG, -1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G);
+                k_y<T, LG, -1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b);
             });
             b.mark("demag_y_fwd");
         }
@@ -617,7 +629,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
                 constexpr int LG = decltype(c)::value;
-                k_y<T, LG, +1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b, p.y_G);
+                k_y<T, LG, +1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b);
             });
             b.mark("demag_y_inv");
         }
