@@ -18,9 +18,9 @@ constexpr int kXThreads = 256;
 // y and z passes: 512-thread blocks, two per SM in FP32 (one block's loads and barriers overlap the
 // other's arithmetic); the longest y lines (2^11) take 1024 threads so that a block still spans 4 columns.
 template <typename T, int LG = 0>
-constexpr int kMaxThreads = (sizeof(T) == 4 && LG >= 11) ? 1024 : 512;
+constexpr int kMaxThreads = 512;
 template <typename T, int LG = 0>
-constexpr int kMinBlocks = (sizeof(T) == 4 && LG < 11) ? 2 : 1;
+constexpr int kMinBlocks = sizeof(T) == 4 ? 2 : 1;
 // values per thread per FFT stage in the y passes: radix-16 stages for the long FP32 lines
 template <typename T, int LG>
 constexpr int kYEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
