@@ -9,6 +9,10 @@
 // straight from global memory (the zero padding is never read); the y and z passes stage their strided
 // tiles in shared memory with cp.async (all copies of a tile in flight at once).  Every pass writes its
 // output from the last FFT stage straight to global memory, and only the part that later passes read.
+//
+// Templates only: demag_f32.cu and demag_f64.cu instantiate them (two translation units, compiled in
+// parallel).
+#pragma once
 #include "demag.cuh"
 #include "fft3.cuh"
 
@@ -500,14 +504,6 @@ static void init_attributes_t()
     });
 }
 
-void demag_init_attributes()
-{
-    static bool done = false;
-    if (done) return;
-    init_attributes_t<float>();
-    init_attributes_t<double>();
-    done = true;
-}
 
 static int pow2_floor(long v)
 {
@@ -532,7 +528,6 @@ DemagPlan demag_plan(const Geom &g)
     p.ok = true;
     const size_t cs = sizeof(Cx<T>);
     const long budget = 8L * kMaxThreads<T>;
-    const int Gmin = (int)(64 / cs);
     if (g.P1 > 1) {
         const int xept = (sizeof(T) == 4 && g.lgQ >= 10) ? 16 : 8;
         int lpb = (int)((long)xept * kXThreads / g.Q);
@@ -662,12 +657,5 @@ void demag_cells(const Geom &g, const DemagBufs<T> &b, const T *M, T *H, cudaStr
 {
     run_pipeline<T, true>(g, b, M, H, st);
 }
-
-template DemagPlan demag_plan<float>(const Geom &);
-template DemagPlan demag_plan<double>(const Geom &);
-template void demag_forward<float>(const Geom &, const DemagBufs<float> &, const float *, float *, cudaStream_t);
-template void demag_forward<double>(const Geom &, const DemagBufs<double> &, const double *, double *, cudaStream_t);
-template void demag_cells<float>(const Geom &, const DemagBufs<float> &, const float *, float *, cudaStream_t);
-template void demag_cells<double>(const Geom &, const DemagBufs<double> &, const double *, double *, cudaStream_t);
 
 }  // namespace nm
