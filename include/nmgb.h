@@ -132,6 +132,11 @@ int nm_llg_step(nm_mesh mesh, int method, double *t, double *dt, double rtol, do
  * Asynchronous: read results with nm_get_state or nm_get_counters. */
 int nm_run_steps(nm_mesh mesh, int method, long n_steps, double rtol, double atol);
 
+/* Volume-weighted mean of the resident m (weights: lumped nodal volume Σ_{c∋n} V/8 over magnetic cells),
+ * the observable of the paper's standard-problem validation and of nm_run_until's samples.  out: HOST
+ * FP64 array of 3.  Synchronises.  Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_CUDA. */
+int nm_mean_m(nm_mesh mesh, double *out);
+
 /* Accepted/rejected step counters and the last error norm (synchronises). Pointers may be NULL. */
 int nm_get_counters(nm_mesh mesh, long *n_accepted, long *n_rejected, double *last_err);
 

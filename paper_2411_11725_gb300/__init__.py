@@ -87,6 +87,7 @@ SIGNATURES = [
     ("nm_llg_step", _i, [_vp, _i, _Pd, _Pd, _d, _d, _Pi]),
     ("nm_run_steps", _i, [_vp, _i, _l, _d, _d]),
     ("nm_get_counters", _i, [_vp, _Pl, _Pl, _Pd]),
+    ("nm_mean_m", _i, [_vp, _Pd]),
     ("nm_run_until", _i, [_vp, _d, _i, _d, _d, _d, _d, _Pd, _l, _Pl, _Pl]),
     ("nm_mesh_info", _i, [_vp, _Pl, _Pl, _Pi, _Pl]),
     ("nm_profile_step", _i, [_vp, _i, _i, _d, _d, _i, _Pd, ctypes.c_char_p, _Pi]),
@@ -263,6 +264,12 @@ class Mesh:
         _check(self.lib.nm_get_state(self._h, ctypes.c_void_p(out.data_ptr()), MEM_HOST, ctypes.byref(t),
                                      ctypes.byref(dt)))
         return t.value, dt.value
+
+    def mean_m(self):
+        """Volume-weighted mean of the resident m (numpy array of 3)."""
+        out = np.zeros(3)
+        _check(self.lib.nm_mean_m(self._h, _pd(out)))
+        return out
 
     def counters(self):
         a, r, e = ctypes.c_long(), ctypes.c_long(), ctypes.c_double()

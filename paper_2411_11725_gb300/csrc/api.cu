@@ -95,6 +95,28 @@ static void fill_twiddles(int twlg, std::vector<Cx<T>> &tw)
     }
 }
 
+// Device address of page-locked host memory that kernels may access directly, or NULL (pageable
+// memory, or memory the current device cannot map).
+void *mapped_host(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    int can_map = 0, unified = 0;
+    cudaDeviceGetAttribute(&can_map, cudaDevAttrCanMapHostMemory, dev);
+    cudaDeviceGetAttribute(&unified, cudaDevAttrUnifiedAddressing, dev);
+    if (!can_map || !unified) return nullptr;
+    return a.devicePointer;
+}
+
 int dev_alloc(nm_mesh M, void **p, size_t bytes)
 {
     cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
@@ -487,9 +509,14 @@ extern "C" int nm_set_state(nm_mesh M, const double *m, int where, double t, dou
     const double *src = m;
     double *tmp = nullptr;
     if (where == NM_MEM_HOST) {
-        CUDA_TRY(cudaMallocAsync(&tmp, g.n_nodes * 3 * sizeof(double), M->st));
-        CUDA_TRY(cudaMemcpyAsync(tmp, m, g.n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, M->st));
-        src = tmp;
+        const void *mapped = mapped_host(m);
+        if (mapped) {
+            src = (const double *)mapped;  // page-locked: the conversion reads it over the link directly
+        } else {
+            CUDA_TRY(cudaMallocAsync(&tmp, g.n_nodes * 3 * sizeof(double), M->st));
+            CUDA_TRY(cudaMemcpyAsync(tmp, m, g.n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, M->st));
+            src = tmp;
+        }
     }
     launch_aos_to_soa<double, double>(g, src, M->m, M->st);
     CHECK_LAUNCH();
@@ -538,6 +565,10 @@ extern "C" int nm_get_state(nm_mesh M, double *m_out, int where, double *t, doub
     if (m_out) {
         if (where == NM_MEM_DEVICE) {
             launch_soa_to_aos<double, double>(g, M->m, m_out, M->st);
+            CHECK_LAUNCH();
+        } else if (void *mapped = mapped_host(m_out)) {
+            // page-locked: the conversion writes it over the link directly
+            launch_soa_to_aos<double, double>(g, M->m, (double *)mapped, M->st);
             CHECK_LAUNCH();
         } else {
             double *tmp = nullptr;
@@ -810,6 +841,14 @@ static int record_mean(nm_mesh M, double *out3)
     CUDA_TRY(cudaStreamSynchronize(M->st));
     for (int j = 0; j < 3; ++j) out3[j] = M->mean_h[j];
     return NM_OK;
+}
+
+extern "C" int nm_mean_m(nm_mesh M, double *out)
+{
+    g_last_error.clear();
+    if (!M || !out) return fail(NM_ERR_ARG, "mesh and out are required");
+    if (!M->state_set) return fail(NM_ERR_STATE, "no state set");
+    return record_mean(M, out);
 }
 
 extern "C" int nm_run_until(nm_mesh M, double t_end, int method, double rtol, double atol, double dt0,

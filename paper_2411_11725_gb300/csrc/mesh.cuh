@@ -105,6 +105,7 @@ struct nm_mesh_s {
 
 
 int dev_alloc(nm_mesh M, void **p, size_t bytes);
+void *mapped_host(const void *p);  // device address of mapped page-locked host memory, or NULL
 // nm_create_mesh; with tensor_src a mesh of the same shape, cell size and precision, the twiddles and
 // the tensor spectrum are copied from it on the device instead of being rebuilt
 int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, void *cuda_stream,

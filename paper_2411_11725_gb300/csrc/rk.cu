@@ -256,35 +256,65 @@ __global__ void __launch_bounds__(1024) k_mean_final(const double *partials, int
     }
 }
 
-// Boundary layout (n1, n2, n3, comp) <-> internal SoA comp-planes with n1 fastest.
+// Boundary layout (n1, n2, n3, comp) <-> internal SoA comp-planes with n1 fastest: a transpose of the
+// n1 and n3 axes for each n2, through 32 x 32 shared-memory tiles so that both sides are accessed in
+// contiguous runs (the boundary side may be page-locked host memory read or written over the
+// host-device link).  Block (32, 8); grid (tiles along n3, tiles along n1, nn2).
+constexpr int kTT = 32;
 template <typename Tin, typename Tout>
-__global__ void k_aos_to_soa(Geom g, const Tin *__restrict__ a, Tout *__restrict__ s)
+__global__ void __launch_bounds__(256) k_aos_to_soa(Geom g, const Tin *__restrict__ a, Tout *__restrict__ s)
 {
-    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (n >= g.n_nodes) return;
-    const int n1 = (int)(n % g.nn1);
-    const long r = n / g.nn1;
-    const int n2 = (int)(r % g.nn2);
-    const int n3 = (int)(r / g.nn2);
-    long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
-    s[n] = (Tout)a[b];
-    s[g.ns + n] = (Tout)a[b + 1];
-    s[2 * g.ns + n] = (Tout)a[b + 2];
+    __shared__ Tout tile[3][kTT][kTT + 1];
+    const int n2 = blockIdx.z;
+    const int n3_0 = blockIdx.x * kTT, n1_0 = blockIdx.y * kTT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < kTT; r += 8) {
+        const int n1 = n1_0 + r, n3 = n3_0 + tx;
+        if (n1 < g.nn1 && n3 < g.nn3) {
+            const long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
+            tile[0][r][tx] = (Tout)a[b];
+            tile[1][r][tx] = (Tout)a[b + 1];
+            tile[2][r][tx] = (Tout)a[b + 2];
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < kTT; r += 8) {
+        const int n3 = n3_0 + r, n1 = n1_0 + tx;
+        if (n1 < g.nn1 && n3 < g.nn3) {
+            const long n = ((long)n3 * g.nn2 + n2) * g.nn1 + n1;
+            s[n] = tile[0][tx][r];
+            s[g.ns + n] = tile[1][tx][r];
+            s[2 * g.ns + n] = tile[2][tx][r];
+        }
+    }
 }
 
 template <typename Tin, typename Tout>
-__global__ void k_soa_to_aos(Geom g, const Tin *__restrict__ s, Tout *__restrict__ a)
+__global__ void __launch_bounds__(256) k_soa_to_aos(Geom g, const Tin *__restrict__ s, Tout *__restrict__ a)
 {
-    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (n >= g.n_nodes) return;
-    const int n1 = (int)(n % g.nn1);
-    const long r = n / g.nn1;
-    const int n2 = (int)(r % g.nn2);
-    const int n3 = (int)(r / g.nn2);
-    long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
-    a[b] = (Tout)s[n];
-    a[b + 1] = (Tout)s[g.ns + n];
-    a[b + 2] = (Tout)s[2 * g.ns + n];
+    __shared__ Tout tile[3][kTT][kTT + 1];
+    const int n2 = blockIdx.z;
+    const int n3_0 = blockIdx.x * kTT, n1_0 = blockIdx.y * kTT;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int r = ty; r < kTT; r += 8) {
+        const int n3 = n3_0 + r, n1 = n1_0 + tx;
+        if (n1 < g.nn1 && n3 < g.nn3) {
+            const long n = ((long)n3 * g.nn2 + n2) * g.nn1 + n1;
+            tile[0][tx][r] = (Tout)s[n];
+            tile[1][tx][r] = (Tout)s[g.ns + n];
+            tile[2][tx][r] = (Tout)s[2 * g.ns + n];
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < kTT; r += 8) {
+        const int n1 = n1_0 + r, n3 = n3_0 + tx;
+        if (n1 < g.nn1 && n3 < g.nn3) {
+            const long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
+            a[b] = tile[0][r][tx];
+            a[b + 1] = tile[1][r][tx];
+            a[b + 2] = tile[2][r][tx];
+        }
+    }
 }
 
 // Cell fields: boundary (c1, c2, c3[, comp]) -> internal c1-fastest (SoA planes for vectors).
@@ -391,13 +421,15 @@ void launch_mean(const Geom &g, const double *m, const T *vol, double *partials,
 template <typename Tin, typename Tout>
 void launch_aos_to_soa(const Geom &g, const Tin *a, Tout *s, cudaStream_t st)
 {
-    k_aos_to_soa<Tin, Tout><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g, a, s);
+    const dim3 grid(div_up(g.nn3, kTT), div_up(g.nn1, kTT), g.nn2);
+    k_aos_to_soa<Tin, Tout><<<grid, dim3(kTT, 8), 0, st>>>(g, a, s);
 }
 
 template <typename Tin, typename Tout>
 void launch_soa_to_aos(const Geom &g, const Tin *s, Tout *a, cudaStream_t st)
 {
-    k_soa_to_aos<Tin, Tout><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g, s, a);
+    const dim3 grid(div_up(g.nn3, kTT), div_up(g.nn1, kTT), g.nn2);
+    k_soa_to_aos<Tin, Tout><<<grid, dim3(kTT, 8), 0, st>>>(g, s, a);
 }
 
 template <typename Tout>

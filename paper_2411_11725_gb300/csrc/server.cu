@@ -258,7 +258,10 @@ int enqueue_copy_out(Run *r)
 {
     nm_mesh M = r->slot->M;
     const Geom &g = M->g;
-    if (r->req.m_out) {
+    if (void *mapped = r->req.m_out ? mapped_host(r->req.m_out) : nullptr) {
+        launch_soa_to_aos<double, double>(g, M->m, (double *)mapped, M->st);  // page-locked: written directly
+        CHECK_LAUNCH();
+    } else if (r->req.m_out) {
         double *tmp = nullptr;
         CUDA_TRY(cudaMallocAsync(&tmp, g.n_nodes * 3 * sizeof(double), M->st));
         launch_soa_to_aos<double, double>(g, M->m, tmp, M->st);

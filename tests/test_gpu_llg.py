@@ -139,3 +139,45 @@ def test_norm_preserved_with_renormalisation(nmgb):
     assert t > 0
     assert np.abs(np.linalg.norm(m, axis=-1) - 1).max() < 1e-12
     me.close()
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_mean_m_is_volume_weighted_mean(nmgb, precision):
+    """nm_mean_m against the weighted mean of the read-back state, weights Σ_{c∋n} V/8 over magnetic
+    cells (computed here from the cell map), on a problem with vacuum cells."""
+    rng = np.random.default_rng(71)
+    p = inp.random_problem(rng, (9, 7, 3), vacuum=True)
+    me = gpu_mesh(nmgb, p, precision)
+    me.set_state(p.m0, 0.0, 1e-14)
+    me.run_steps(3, nmgb.DP54, 1e-5, 1e-5)
+    m, _, _ = me.get_state()
+    mag = (p.Ms_cells() > 0).astype(float)
+    w = np.zeros(p.nodes)
+    for i in range(2):
+        for j in range(2):
+            for k in range(2):
+                w[i:i + p.n[0], j:j + p.n[1], k:k + p.n[2]] += mag
+    ref = (w[..., None] * m).sum((0, 1, 2)) / w.sum()
+    got = me.mean_m()
+    me.close()
+    # FP32 meshes keep the volume weights in FP32 (relative rounding 6e-8)
+    assert np.abs(got - ref).max() < (1e-12 if precision == 1 else 1e-7)
+
+
+def test_state_round_trip_through_page_locked_memory(nmgb):
+    """Page-locked host buffers are read and written by the layout kernels directly; pageable ones go
+    through a device copy.  Both give the same state, bit for bit."""
+    import torch
+    rng = np.random.default_rng(72)
+    p = inp.random_problem(rng, (33, 9, 34), vacuum=False)
+    me = gpu_mesh(nmgb, p, 0)
+    pinned_in = torch.from_numpy(p.m0.copy()).pin_memory()
+    me.set_state_host_ptr(pinned_in, 0.0, 1e-14)
+    m_pageable, _, _ = me.get_state()
+    assert np.array_equal(m_pageable, p.m0)
+    me.run_steps(2, nmgb.DP54, 1e-5, 1e-5)
+    pinned_out = torch.empty_like(pinned_in).pin_memory()
+    me.get_state_host_ptr(pinned_out)
+    m_pageable, _, _ = me.get_state()
+    assert np.array_equal(pinned_out.numpy(), m_pageable)
+    me.close()
