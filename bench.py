@@ -188,6 +188,37 @@ def traffic_for(name, workload_key):
     return float(v) * (scale if scale else 1.0) if (scale or ent.get("workload") == workload_key) else None
 
 
+class RankReducer:
+    """Max / sum of a scalar over the ranks of a process group (or the value itself without one), and a
+    barrier.  Timing takes the max over ranks; counts are summed."""
+
+    def __init__(self, dist=None, device="cuda"):
+        self.dist, self.device = dist, device
+
+    def _reduce(self, x, op):
+        if self.dist is None:
+            return float(x)
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=op)
+        return float(t.item())
+
+    def max(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.MAX)
+
+    def sum(self, x):
+        return self._reduce(x, None if self.dist is None else self.dist.ReduceOp.SUM)
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+
+def whole_job_rate(red, units_per_item, items_this_rank, seconds_this_rank):
+    """Aggregate rate of all ranks: units processed by all ranks / the slowest rank's time."""
+    return units_per_item * red.sum(items_this_rank) / red.max(seconds_this_rank)
+
+
 # ----------------------------------------------------------------------------------------- arms
 def oracle_sample(seconds=15.0, grid=(32, 32, 4), max_steps=None):
     """Time the FP64 oracle (direct-sum demag) on a bounded sample: DP5 steps on a smaller cuboid of
@@ -267,9 +298,10 @@ def run_ours(args, rank, world, dist):
         me.set_state(m0, 0.0, 1e-15)
         return me
 
+    red = RankReducer(dist, "cuda")
+
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        red.barrier()
 
     def timed_steps(me, k):
         torch.cuda.synchronize()
@@ -288,19 +320,8 @@ def run_ours(args, rank, world, dist):
         a1, r1, err = me.counters()
         return ms, a1 - a0, r1 - r0
 
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    max_over_ranks = red.max
+    sum_over_ranks = red.sum
 
     # ---- FP32 (mixed) path: the headline
     me = make(nmgb.F32)
@@ -310,9 +331,9 @@ def run_ours(args, rank, world, dist):
     clk.start()
     ms, acc, rej = timed_steps(me, K)
     clocks = clk.stop()
+    value = whole_job_rate(red, nn, acc, ms * 1e-3)
     ms_max = max_over_ranks(ms)
     acc_tot = sum_over_ranks(acc)
-    value = nn * acc_tot / (ms_max * 1e-3)
     # per-launch timing for the roofline (CUDA events between launches on the mesh stream)
     prof = me.profile_step(nmgb.DP54, reps=3)
     # ---- e2e: the public API with host buffers, every step: H2D of m, one step, D2H of m
