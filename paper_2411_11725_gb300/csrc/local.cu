@@ -293,7 +293,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 // STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
 // input.  Block (bx, by, bz) covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [bz*zc, bz*zc+zc).
 template <typename T, bool STAGE>
-__global__ void __launch_bounds__(kTX *kTY<T>, 3) k_node(LocalParams<T> p, const T *__restrict__ y,
+__global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 4 : 3) k_node(LocalParams<T> p, const T *__restrict__ y,
                                                         T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
                                                         double t_heff, int zc)
 {
