@@ -188,11 +188,14 @@ int nm_h_eff_vjp(nm_mesh mesh, const void *m, const void *v, unsigned terms, dou
  * section "Automatic Differentiation and Time Integration"), recomputing segments of
  * `checkpoint_every` steps from stored states (<= 0: 32).  weight, target: HOST FP64 nodal vector
  * fields (target may be NULL = 0).  Outputs (HOST FP64, each may be NULL except loss): loss; grad_Ms
- * (cell scalar field, dL/dMs); grad_m0 (nodal vector field, dL/dm(t0)); n_steps (accepted steps).
+ * (cell scalar field, dL/dMs); grad_m0 (nodal vector field, dL/dm(t0)); n_steps (accepted steps);
+ * grad_h (3 values: dL/dh of the uniform applied field amplitude of nm_set_field, the design variable of
+ * the paper's field-angle inverse problem, section "Inverse Problems").
  * The resident state ends at t_end.  Synchronises.  Errors: as nm_run_until, NM_ERR_OOM. */
 int nm_adjoint_run(nm_mesh mesh, int method, double t_end, double rtol, double atol, double dt0,
                    double sample_dt, const double *weight, const double *target, int include_initial,
-                   long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps);
+                   long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps,
+                   double *grad_h);
 
 /* Sizes of the mesh: nodes, cells, padded FFT lengths P1 P2 P3, and the device bytes the mesh holds. */
 int nm_mesh_info(nm_mesh mesh, long *n_nodes, long *n_cells, int P[3], long *device_bytes);

@@ -92,7 +92,7 @@ SIGNATURES = [
     ("nm_mesh_info", _i, [_vp, _Pl, _Pl, _Pi, _Pl]),
     ("nm_profile_step", _i, [_vp, _i, _i, _d, _d, _i, _Pd, ctypes.c_char_p, _Pi]),
     ("nm_h_eff_vjp", _i, [_vp, _vp, _vp, _u, _d, _vp, _vp]),
-    ("nm_adjoint_run", _i, [_vp, _i, _d, _d, _d, _d, _d, _Pd, _Pd, _i, _l, _Pd, _Pd, _Pd, _Pl]),
+    ("nm_adjoint_run", _i, [_vp, _i, _d, _d, _d, _d, _d, _Pd, _Pd, _i, _l, _Pd, _Pd, _Pd, _Pl, _Pd]),
     ("nm_footprint_bytes", _l, [_i, _i, _i, _i]),
     ("nm_sync", _i, [_vp]),
     ("nm_server_create", _i, [_l, _i, ctypes.POINTER(_vp)]),
@@ -213,6 +213,11 @@ class Mesh:
         _check(self.lib.nm_set_field(self._h, FIELD_HEXT_UNIFORM, None, _pd(hu), float(freq), float(phase)))
         hc = None if h_cell is None else _host_f64(h_cell, self.n + (3,))
         _check(self.lib.nm_set_field(self._h, FIELD_HEXT_CELL, _pd(hc), None, float(cell_freq), float(cell_phase)))
+
+    def set_uniform_field(self, h_uniform, freq=0.0, phase=0.0):
+        """Set the uniform applied field (A/m) only, leaving any cell-wise field in place."""
+        hu = _host_f64(h_uniform, (3,))
+        _check(self.lib.nm_set_field(self._h, FIELD_HEXT_UNIFORM, None, _pd(hu), float(freq), float(phase)))
 
     def set_terms(self, terms):
         _check(self.lib.nm_set_terms(self._h, int(terms)))
@@ -340,19 +345,23 @@ class Mesh:
         return gm, gMs
 
     def adjoint_run(self, t_end, weight, target=None, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0,
-                    sample_dt=0.0, include_initial=False, checkpoint_every=32):
+                    sample_dt=0.0, include_initial=False, checkpoint_every=32, field_grad=False):
         """Forward integration to t_end with the sampled quadratic loss and its discrete adjoint.
-        Returns (loss, dL/dMs (N1,N2,N3), dL/dm0 nodal, accepted steps)."""
+        Returns (loss, dL/dMs (N1,N2,N3), dL/dm0 nodal, accepted steps), and dL/dh of the uniform applied
+        field (3,) as a fifth element when field_grad is set."""
         W = _host_f64(weight, self.nodes + (3,))
         tg = None if target is None else _host_f64(target, self.nodes + (3,))
         loss = ctypes.c_double()
         gMs = np.zeros(self.n)
         gm0 = np.zeros(self.nodes + (3,))
+        gh = np.zeros(3) if field_grad else None
         ns = ctypes.c_long()
         _check(self.lib.nm_adjoint_run(self._h, int(method), float(t_end), float(rtol), float(atol), float(dt0),
                                        float(sample_dt), _pd(W), _pd(tg), int(bool(include_initial)),
                                        int(checkpoint_every), ctypes.byref(loss), _pd(gMs), _pd(gm0),
-                                       ctypes.byref(ns)))
+                                       ctypes.byref(ns), _pd(gh)))
+        if field_grad:
+            return loss.value, gMs, gm0, ns.value, gh
         return loss.value, gMs, gm0, ns.value
 
     def run_until(self, t_end, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0, sample_dt=0.0):

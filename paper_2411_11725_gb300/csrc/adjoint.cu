@@ -247,6 +247,9 @@ void llg_vjp(nm_mesh M, const T *y, double t, const T *u, T *ybar)
     field_at<T>(M, y, M->terms, t, (T *)M->vj_h);
     launch_llg_vjp_local<T>(g, y, (const T *)M->vj_h, u, (const T *)M->inv_mass,
                             M->gamma / (1.0 + M->alpha * M->alpha), M->alpha, ybar, (T *)M->vj_q, M->st);
+    // the uniform applied field adds h s(t) to H at every magnetic node: dL/dh += s(t) sum_n q_n
+    if (M->vj_gh && (M->terms & NM_ZEE))
+        launch_accum_nodal<T>(g, (const T *)M->vj_q, host_time_factor(M->hu_freq, M->hu_phase, t), M->vj_gh, M->st);
     heff_vjp_core<T>(M, y, (const T *)M->vj_q, (const T *)M->vj_h, M->terms, t, (T *)M->vj_g, M->vj_gMs, 1.0);
     launch_axpby<T>(g, T(1), ybar, T(1), (const T *)M->vj_g, ybar, M->st);
 }
@@ -323,7 +326,7 @@ int sample_loss(nm_mesh M, const double *W, const double *tgt, double *lam, AdjB
 template <typename T>
 int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol, double dt0, double sample_dt,
                   const double *weight, const double *target, int include_initial, long C, double *loss_out,
-                  double *grad_Ms, double *grad_m0, long *n_steps_out)
+                  double *grad_Ms, double *grad_m0, long *n_steps_out, double *grad_h)
 {
     const Geom &g = M->g;
     const size_t nb3 = 3 * g.ns * sizeof(T), nd3 = 3 * g.ns * sizeof(double);
@@ -360,6 +363,7 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
         return NM_OK;
     };
     auto release_all = [&]() {
+        M->vj_gh = nullptr;
         for (void *p : owned) cudaFreeAsync(p, M->st);
         owned.clear();
     };
@@ -383,6 +387,12 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
     ADJ_TRY(galloc((void **)&A.lamt, nd3));
     ADJ_TRY(galloc((void **)&A.partials, 1024 * sizeof(double)));
     ADJ_TRY(galloc((void **)&A.scalar, sizeof(double)));
+    if (grad_h) {
+        double *gh = nullptr;
+        ADJ_TRY(galloc((void **)&gh, nd3));
+        CUDA_TRY(cudaMemsetAsync(gh, 0, nd3, M->st));
+        M->vj_gh = gh;  // llg_vjp accumulates the uniform-field gradient here
+    }
     double *W = nullptr, *tgt = nullptr, *tmp = nullptr;
     ADJ_TRY(galloc((void **)&W, nd3));
     ADJ_TRY(galloc((void **)&tmp, g.n_nodes * 3 * sizeof(double)));
@@ -546,6 +556,13 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
         launch_soa_to_aos<double, double>(g, A.lam, tmp, M->st);
         CUDA_TRY(cudaMemcpyAsync(grad_m0, tmp, g.n_nodes * 3 * sizeof(double), cudaMemcpyDeviceToHost, M->st));
     }
+    if (grad_h) {
+        launch_sum_nodal3(g, M->vj_gh, M->partials, M->mean_d, M->st);
+        CHECK_LAUNCH();
+        CUDA_TRY(cudaMemcpyAsync(M->mean_h, M->mean_d, 3 * sizeof(double), cudaMemcpyDeviceToHost, M->st));
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+        for (int c = 0; c < 3; ++c) grad_h[c] = M->mean_h[c];
+    }
     // leave the resident state at the end of the forward run (k1 recomputed on the next step)
     CUDA_TRY(cudaMemcpyAsync(M->m, m_end, nd3, cudaMemcpyDeviceToDevice, M->st));
     ADJ_TRY(set_ctl(M, t_final, dt_final));
@@ -564,7 +581,8 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
 
 extern "C" int nm_adjoint_run(nm_mesh M, int method, double t_end, double rtol, double atol, double dt0,
                               double sample_dt, const double *weight, const double *target, int include_initial,
-                              long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps)
+                              long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps,
+                              double *grad_h)
 {
     int rc = check_step_args(M, method, rtol, atol);
     if (rc) return rc;
@@ -574,7 +592,7 @@ extern "C" int nm_adjoint_run(nm_mesh M, int method, double t_end, double rtol, 
     if (checkpoint_every < 1) checkpoint_every = 32;
     return M->prec == NM_F64
                ? adjoint_run_t<double>(M, method, t_end, rtol, atol, dt0, sample_dt, weight, target, include_initial,
-                                       checkpoint_every, loss, grad_Ms, grad_m0, n_steps)
+                                       checkpoint_every, loss, grad_Ms, grad_m0, n_steps, grad_h)
                : adjoint_run_t<float>(M, method, t_end, rtol, atol, dt0, sample_dt, weight, target, include_initial,
-                                      checkpoint_every, loss, grad_Ms, grad_m0, n_steps);
+                                      checkpoint_every, loss, grad_Ms, grad_m0, n_steps, grad_h);
 }

@@ -95,6 +95,7 @@ struct nm_mesh_s {
     void *vj_w = nullptr, *vj_h = nullptr, *vj_q = nullptr, *vj_g = nullptr;      // nodal 3 x ns
     void *vj_H = nullptr, *vj_HW = nullptr, *vj_M = nullptr;                      // cells 3 x cs
     double *vj_gMs = nullptr;                                                    // cells, FP64 accumulator
+    double *vj_gh = nullptr;  // nodal FP64 accumulator of the uniform-field gradient (during nm_adjoint_run)
     std::vector<void *> extra;                                                   // further adjoint buffers
     // per-launch profiling (nm_profile_step)
     bool prof_on = false;

@@ -313,6 +313,49 @@ void launch_sum_partials(const double *partials, int n, double *out, cudaStream_
     k_sum_partials<<<1, 1024, 0, st>>>(partials, n, out);
 }
 
+template <typename T>
+__global__ void k_accum_nodal(long n_nodes, long ns, const T *__restrict__ q, double scale, double *__restrict__ acc)
+{
+    long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= n_nodes) return;
+    for (int c = 0; c < 3; ++c) acc[c * ns + n] += scale * (double)q[c * ns + n];
+}
+
+template <typename T>
+void launch_accum_nodal(const Geom &g, const T *q, double scale, double *acc, cudaStream_t st)
+{
+    k_accum_nodal<T><<<(int)((g.n_nodes + 255) / 256), 256, 0, st>>>(g.n_nodes, g.ns, q, scale, acc);
+}
+
+__global__ void __launch_bounds__(256) k_sum_nodal3_partials(long n_nodes, long ns, const double *__restrict__ acc,
+                                                              double *partials)
+{
+    __shared__ double sh[3][256];
+    double v[3] = {0.0, 0.0, 0.0};
+    for (long n = blockIdx.x * (long)blockDim.x + threadIdx.x; n < n_nodes; n += (long)gridDim.x * blockDim.x)
+        for (int c = 0; c < 3; ++c) v[c] += acc[c * ns + n];
+    for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] = v[c];
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) partials[c * 1024 + blockIdx.x] = sh[c][0];
+}
+
+void launch_sum_nodal3(const Geom &g, const double *acc, double *partials, double *out, cudaStream_t st)
+{
+    long b = (g.n_nodes + 255) / 256;
+    const int nb = (int)(b > 1024 ? 1024 : b);
+    k_sum_nodal3_partials<<<nb, 256, 0, st>>>(g.n_nodes, g.ns, acc, partials);
+    for (int c = 0; c < 3; ++c) k_sum_partials<<<1, 1024, 0, st>>>(partials + c * 1024, nb, out + c);
+}
+
+template void launch_accum_nodal<float>(const Geom &, const float *, double, double *, cudaStream_t);
+template void launch_accum_nodal<double>(const Geom &, const double *, double, double *, cudaStream_t);
+
 #define NM_ADJ_INST(T)                                                                                          \
     template void launch_lincomb<T>(const Geom &, const LinComb &, T *, cudaStream_t);                          \
     template void launch_lincomb_d<T>(const Geom &, const LinComb &, double *, cudaStream_t);                   \

@@ -81,4 +81,10 @@ int launch_loss_terms(const Geom &g, const double *m, const double *W, const dou
 // sum of the first n partials into out[0] (one block, fixed order)
 void launch_sum_partials(const double *partials, int n, double *out, cudaStream_t st);
 
+// acc[c][n] += scale * q[c][n] (FP64 nodal accumulator of a uniform-field gradient)
+template <typename T>
+void launch_accum_nodal(const Geom &g, const T *q, double scale, double *acc, cudaStream_t st);
+// out[c] = sum_n acc[c][n] (deterministic two-level reduction through partials[3 x 1024])
+void launch_sum_nodal3(const Geom &g, const double *acc, double *partials, double *out, cudaStream_t st);
+
 }  // namespace nm

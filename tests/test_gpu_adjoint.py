@@ -128,3 +128,26 @@ def test_adjoint_checkpoint_interval_does_not_change_gradient(nmgb):
     b = _run(nmgb, p, p.Ms_cells(), W, tgt, dict(kw, checkpoint_every=1000))
     assert a[0] == b[0] and a[3] == b[3]
     assert rel_l2(a[1], b[1]) < 1e-13 and rel_l2(a[2], b[2]) < 1e-13
+
+
+def test_field_gradient_matches_finite_differences(nmgb):
+    """dL/dh of the uniform applied field (frozen step sizes) against central differences."""
+    p, W, tgt, rng = _loss_problem(42)
+    p.h_freq = 0.0
+    kw = dict(t_end=1.2e-13, method=nmgb.DP54, rtol=1e3, atol=1e3, dt0=5e-15, sample_dt=2e-14, checkpoint_every=4)
+
+    def run(h, field_grad=False):
+        me = gpu_mesh(nmgb, p, 1)
+        me.set_uniform_field(h)
+        me.set_state(p.m0, 0.0, 1e-14)
+        out = me.adjoint_run(weight=W, target=tgt, field_grad=field_grad, **kw)
+        me.close()
+        return out
+
+    h0 = np.array(p.h_uniform)
+    loss, _, _, _, gh = run(h0, True)
+    assert loss > 0 and np.abs(gh).max() > 0
+    for _ in range(3):
+        d = rng.standard_normal(3) * 1e-3 * np.linalg.norm(h0)
+        fd = (run(h0 + d)[0] - run(h0 - d)[0]) / 2
+        assert abs(fd - gh @ d) <= 1e-6 * abs(fd) + 1e-12 * loss, (fd, gh @ d)
