@@ -211,6 +211,8 @@ void run_stages(nm_mesh M, const Tableau &tb, AdjBufs<T> &A)
             sa.af[j] = (float)tb.a[s][j];
         }
         sa.s = s;
+        sa.a_s = next ? tb.a[s][s - 1] : 0.0;
+        sa.af_s = (float)sa.a_s;
         sa.c_s = tb.c[s - 1];
         sa.ctl = M->ctl;
         launch_llg_stage<T>(p, ys, (T *)M->k[s - 1], next ? A.Y[s] : nullptr, sa, M->st);

@@ -644,6 +644,8 @@ static void enqueue_stage(nm_mesh M, const LocalParams<T> &p, int s, double c_s,
         sa.af[j] = (float)a_next[j];
     }
     sa.s = s;
+    sa.a_s = n_next >= s ? a_next[s - 1] : 0.0;
+    sa.af_s = (float)sa.a_s;
     sa.c_s = c_s;
     sa.ctl = M->ctl;
     launch_llg_stage<T>(p, ys, (T *)M->k[s - 1], ynext, sa, M->st);

@@ -45,6 +45,7 @@ struct DemagPlan {
     size_t y_smem;
     int z_G, z_KY, z_threads;
     size_t z_smem;
+    bool z_reg;                // FP32, P3 <= 64: the register z convolution (two threads per line)
     int yc_G, yc_threads;
     size_t yc_smem;
 };

@@ -51,7 +51,9 @@ struct ZTile {
     static_assert(NL * P3 <= EPT * THREADS && THREADS <= kMaxThreads<T>, "z tile exceeds the block");
 };
 
-// Compile-time tile of the y passes for lines of 2^LG: G kx columns, EPT values per thread.
+// Compile-time tile of the y passes for lines of 2^LG: G kx columns, EPT values per thread.  Tiles of
+// fewer than 16 columns pad the lines-fastest layout with one row every 8 elements (LFP = 3): the first
+// stage stores with a stride of radix x G elements, which otherwise hits the same banks.
 template <typename T, int LG>
 struct YTile {
     static constexpr int P2 = 1 << LG;
@@ -59,8 +61,9 @@ struct YTile {
     static constexpr int MAXT = kMaxThreads<T, LG>;
     static constexpr int G0 = pow2_floor_c(EPT * MAXT / P2);
     static constexpr int G = G0 > 16 ? 16 : (G0 < 1 ? 1 : G0);
+    static constexpr int LFP = G < 16 ? 3 : 0;
     static constexpr int THREADS = ((G * P2 / EPT > 32 ? G * P2 / EPT : 32) + 31) / 32 * 32;
-    static constexpr size_t SMEM = (size_t)G * P2 * sizeof(Cx<T>);
+    static constexpr size_t SMEM = (size_t)G * f3::lf_rows(P2, LFP) * sizeof(Cx<T>);
     static_assert(G * P2 <= EPT * THREADS && THREADS <= MAXT, "y tile exceeds the block");
 };
 
@@ -283,12 +286,12 @@ __global__ void k_x_inv1(Geom g, DemagBufs<T> b, T *__restrict__ out)
 
 // Passes 2 and 4: y transform of G consecutive kx columns of one (component, z) plane, in place.
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
-// Shared layout: row y at buf + y * G (lines = columns, fastest).
+// Shared layout: row y at buf + lfpad(y) * G (lines = columns, fastest; padded rows for narrow tiles).
 template <typename T, int LG, int DIR>
 __global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geom g, DemagBufs<T> b)
 {
     if (b.ctl && b.ctl->done) return;
-    constexpr int P2 = 1 << LG, G = YTile<T, LG>::G;
+    constexpr int P2 = 1 << LG, G = YTile<T, LG>::G, LFP = YTile<T, LG>::LFP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
@@ -299,13 +302,13 @@ __global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geo
     constexpr int cpr = rowb / cb;  // copies per row
     for (int t = threadIdx.x; t < nin * cpr; t += blockDim.x) {
         const int y = t / cpr, ch = t - y * cpr;
-        cpa_chunk((char *)(buf + y * G) + ch * cb, (const char *)(base + y * Xp) + ch * cb, cb);
+        cpa_chunk((char *)(buf + f3::lfpad<LFP>(y) * G) + ch * cb, (const char *)(base + y * Xp) + ch * cb, cb);
     }
     cpa_wait_all();
     __syncthreads();
     auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    f3::fft<T, LG, DIR, true, true, false, kYEpt<T, LG>, G>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, nout,
-                                                            f3::NoFn<T>(), dst);
+    f3::fft<T, LG, DIR, true, true, false, kYEpt<T, LG>, G, LFP>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, nout,
+                                                                 f3::NoFn<T>(), dst);
 }
 
 // The six real tensor components at octant frequency (kx, a2, kz), with the sign of the odd ones in
@@ -338,6 +341,51 @@ __device__ __forceinline__ void tensor_mul(const Ten6<T> &t, T s2, Cx<T> *px, Cx
     *pz = cx<T>(t.xz * mx.x + nyz * my.x + t.zz * mz.x, t.xz * mx.y + nyz * my.y + t.zz * mz.y);
 }
 
+// ky of row r of a z tile whose octant rows start at a20: rows r < KY are ky = a20 + r, rows KY + r are
+// the mirrors P2 - (a20 + r), present when 0 < a2 < P2/2; -1 marks an absent row
+template <int KY>
+__device__ __forceinline__ int z_row_ky(const Geom &g, int a20, int r)
+{
+    const int a2 = a20 + (r < KY ? r : r - KY);
+    if (a2 >= g.H2) return -1;
+    if (r < KY) return a2;
+    return (a2 > 0 && a2 < (g.P2 >> 1)) ? g.P2 - a2 : -1;
+}
+
+// Stage a z tile in shared memory with cp.async: the N3 spectrum rows of its 3 x 2KY lines of G kx
+// columns (element z of line l = (c * 2KY + r) * G + g at buf[z * nl + l]), then the tensor slice
+// [component][a3][row][kx] behind the NL * P3 spectrum values; ends with a barrier.
+template <typename T, int G, int KY, int P3>
+__device__ __forceinline__ void z_tile_load(const Geom &g, const DemagBufs<T> &b, Cx<T> *buf, int kx0, int a20)
+{
+    constexpr int R2 = 2 * KY, nl = 3 * R2 * G, H3 = P3 / 2 + 1;
+    constexpr int rowb = G * (int)sizeof(Cx<T>);
+    constexpr int cb = rowb >= 16 ? 16 : rowb, lcpr = rowb / cb == 1 ? 0 : (rowb / cb == 2 ? 1 : (rowb / cb == 4 ? 2 : 3));
+    const int nrow = g.N3 * 3 * R2;
+    for (int t = threadIdx.x; t < (nrow << lcpr); t += blockDim.x) {
+        const int rr = t >> lcpr, ch = t - (rr << lcpr);
+        const int r = rr % R2, cz = rr / R2, z = cz / 3, c = cz - 3 * z;
+        const int ky = z_row_ky<KY>(g, a20, r);
+        if (ky < 0) continue;
+        const long ga = c * g.s_comp + ((long)z * g.P2 + ky) * g.Xp + kx0;
+        cpa_chunk((char *)(buf + z * nl + (c * R2 + r) * G) + ch * cb, (const char *)(b.S + ga) + ch * cb, cb);
+    }
+    // the tensor slice of this tile, copied while the spectrum rows arrive
+    T *ten = reinterpret_cast<T *>(buf + nl * P3);
+    constexpr int trowb = G * (int)sizeof(T);
+    constexpr int tcb = trowb >= 16 ? 16 : trowb, tch = trowb / tcb;
+    for (int t = threadIdx.x; t < 6 * H3 * KY * tch; t += blockDim.x) {
+        const int row = t / tch, ch = t - row * tch;
+        const int rr = row % KY, kq = row / KY, a3 = kq % H3, comp = kq / H3;
+        const int a2 = a20 + rr;
+        if (a2 >= g.H2) continue;
+        cpa_chunk((char *)(ten + row * G) + ch * tcb,
+                  (const char *)(b.Nk + comp * g.t_comp + ((long)a3 * g.H2 + a2) * g.Xp + kx0) + ch * tcb, tcb);
+    }
+    cpa_wait_all();
+    __syncthreads();
+}
+
 // Pass 3 (N3 > 1): G kx columns x KY octant rows a2 (each with its mirror P2 - a2, so the tensor is
 // read once): forward z (N3 non-zero inputs), tensor product, inverse z keeping z < N3.
 // Rows r < KY are ky = a2_0 + r, rows KY + r are ky = P2 - (a2_0 + r) (present when 0 < a2 < P2/2).
@@ -353,40 +401,9 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
     const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
     constexpr int R2 = 2 * KY, nl = 3 * R2 * G;
     const int h2 = g.P2 >> 1;
-    auto row_ky = [&](int r) -> int {  // -1: row absent
-        const int a2 = a20 + (r < KY ? r : r - KY);
-        if (a2 >= g.H2) return -1;
-        if (r < KY) return a2;
-        return (a2 > 0 && a2 < h2) ? g.P2 - a2 : -1;
-    };
+    auto row_ky = [&](int r) -> int { return z_row_ky<KY>(g, a20, r); };
     auto gaddr = [&](int c, int ky, int z) -> long { return c * g.s_comp + ((long)z * g.P2 + ky) * g.Xp + kx0; };
-    {
-        constexpr int rowb = G * (int)sizeof(Cx<T>);
-        constexpr int cb = rowb >= 16 ? 16 : rowb, lcpr = rowb / cb == 1 ? 0 : (rowb / cb == 2 ? 1 : (rowb / cb == 4 ? 2 : 3));
-        const int nrow = g.N3 * 3 * R2;
-        for (int t = threadIdx.x; t < (nrow << lcpr); t += blockDim.x) {
-            const int rr = t >> lcpr, ch = t - (rr << lcpr);
-            const int r = rr % R2, cz = rr / R2, z = cz / 3, c = cz - 3 * z;
-            const int ky = row_ky(r);
-            if (ky < 0) continue;
-            cpa_chunk((char *)(buf + z * nl + (c * R2 + r) * G) + ch * cb, (const char *)(b.S + gaddr(c, ky, z)) + ch * cb,
-                      cb);
-        }
-        // the tensor slice of this tile, [component][a3][row][kx], copied while the spectrum rows arrive
-        T *ten = reinterpret_cast<T *>(buf + nl * P3);
-        constexpr int trowb = G * (int)sizeof(T);
-        constexpr int tcb = trowb >= 16 ? 16 : trowb, tch = trowb / tcb;
-        for (int t = threadIdx.x; t < 6 * H3 * KY * tch; t += blockDim.x) {
-            const int row = t / tch, ch = t - row * tch;
-            const int rr = row % KY, kq = row / KY, a3 = kq % H3, comp = kq / H3;
-            const int a2 = a20 + rr;
-            if (a2 >= g.H2) continue;
-            cpa_chunk((char *)(ten + row * G) + ch * tcb,
-                      (const char *)(b.Nk + comp * g.t_comp + ((long)a3 * g.H2 + a2) * g.Xp + kx0) + ch * tcb, tcb);
-        }
-        cpa_wait_all();
-        __syncthreads();
-    }
+    z_tile_load<T, G, KY, P3>(g, b, buf, kx0, a20);
     const FastDiv nlf(1u);  // unused: the line count is a compile-time constant
     f3::fft<T, LG, -1, true, true, true, Z::EPT, nl>(buf, nl, nlf, b.tw, g.twlg, g.N3, P3, f3::NoFn<T>(),
                                                     f3::NoFn<T>());
@@ -422,6 +439,109 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
         if (ky >= 0) b.S[gaddr(c, ky, z) + gg] = v;
     };
     f3::fft<T, LG, +1, true, true, false, Z::EPT, nl>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
+}
+
+// Register z convolution (FP32, P3 = 2^LG <= 64).  The z input is zero above N3 <= P3/2, so the
+// spectrum splits by parity: X_{2k+r} = sum_{n<H} (x_n w^{rn}) e^{-2 pi i nk/H}, w = e^{-2 pi i/P3},
+// H = P3/2, and the inverse kept for z < N3 is y_n = u0_n + conj(w)^n u1_n with u_r the inverse
+// length-H transform of the parity-r half.  Each line gets two threads, one per parity, and each
+// thread runs its whole length-H transform in registers: no shared-memory exchanges between FFT
+// stages.  Shared layout: the tile of z_tile_load; after the forward transform, kz = 2k + r of line l
+// sits in row r*H + k.
+template <int LG>
+struct ZRTile {
+    static constexpr int P3 = 1 << LG, H = P3 / 2, G = 16;
+    static constexpr int KY0 = pow2_floor_c(56 * 1024 / (6 * G * P3 * 8));
+    static constexpr int KY = KY0 < 1 ? 1 : (KY0 > 2 ? 2 : KY0);
+    static constexpr int NL = 6 * KY * G;  // lines (a multiple of 32: warps hold one parity)
+    static constexpr int THREADS = 2 * NL;
+    static constexpr size_t SMEM = (size_t)NL * P3 * sizeof(Cx<float>) + (size_t)6 * (H + 1) * KY * G * sizeof(float);
+    static_assert(LG >= 2 && LG <= 6 && NL % 32 == 0 && THREADS <= 1024, "register z tile");
+};
+
+template <int LG>
+__global__ void __launch_bounds__(ZRTile<LG>::THREADS, LG >= 6 ? 3 : 2) k_z_conv_r(Geom g, DemagBufs<float> b)
+{
+    using T = float;
+    using Z = ZRTile<LG>;
+    if (b.ctl && b.ctl->done) return;
+    constexpr int P3 = Z::P3, H = Z::H, H3 = H + 1, G = Z::G, KY = Z::KY, R2 = 2 * KY, nl = Z::NL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
+    const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
+    z_tile_load<T, G, KY, P3>(g, b, buf, kx0, a20);
+    const int par = threadIdx.x >= nl ? 1 : 0, l = threadIdx.x - par * nl;
+    const int N3 = g.N3;
+    {
+        // forward: parity par of the line's spectrum
+        Cx<T> v[H];
+#pragma unroll
+        for (int n = 0; n < H; ++n) v[n] = n < N3 ? buf[n * nl + l] : cx<T>(T(0), T(0));
+        __syncthreads();  // both parities have read the input rows before either overwrites them
+        if (par) {
+#pragma unroll
+            for (int n = 1; n < H; ++n) v[n] = f3::rot<T, P3, -1>(v[n], n);
+        }
+        f3::dft_reg<T, H, -1>(v);
+#pragma unroll
+        for (int k = 0; k < H; ++k) buf[(par * H + k) * nl + l] = v[f3::bitrev<H>(k)];
+    }
+    __syncthreads();
+    {
+        // H^ = N~ M^ at every (kz, row, kx) of the tile; row q holds kz = 2 (q mod H) + q / H
+        const T *ten = reinterpret_cast<const T *>(buf + nl * P3);
+        constexpr int tstride = H3 * KY * G, npts = KY * G * P3;
+        const int h2 = g.P2 >> 1;
+#pragma unroll 2
+        for (int t = threadIdx.x; t < npts; t += Z::THREADS) {
+            const int gg = t % G, qr = t / G, rr = qr % KY, q = qr / KY;
+            const int a2 = a20 + rr;
+            if (a2 >= g.H2) continue;
+            const int kz = q < H ? 2 * q : 2 * (q - H) + 1;
+            const int a3 = kz <= H ? kz : P3 - kz;
+            const T s3 = kz <= H ? T(1) : T(-1);
+            const T *tp = ten + (a3 * KY + rr) * G + gg;
+            Ten6<T> tt;
+            tt.xx = tp[0];
+            tt.yy = tp[tstride];
+            tt.zz = tp[2 * tstride];
+            tt.xy = tp[3 * tstride];
+            tt.xz = tp[4 * tstride] * s3;
+            tt.yz = tp[5 * tstride] * s3;
+            Cx<T> *p = buf + q * nl + rr * G + gg;
+            tensor_mul(tt, T(1), p, p + R2 * G, p + 2 * R2 * G);
+            if (a2 > 0 && a2 < h2) {
+                Cx<T> *pm = p + KY * G;
+                tensor_mul(tt, T(-1), pm, pm + R2 * G, pm + 2 * R2 * G);
+            }
+        }
+    }
+    __syncthreads();
+    {
+        // inverse: u_par from rows par*H.., twisted by conj(w)^n for the odd parity; the odd threads
+        // leave their part in their own (consumed) rows, the even threads add it and store z < N3
+        Cx<T> v[H];
+#pragma unroll
+        for (int k = 0; k < H; ++k) v[k] = buf[(par * H + k) * nl + l];
+        f3::dft_reg<T, H, +1>(v);
+        if (par) {
+#pragma unroll
+            for (int n = 0; n < H; ++n)
+                if (n < N3) buf[(H + n) * nl + l] = f3::rot<T, P3, +1>(v[f3::bitrev<H>(n)], n);
+        }
+        __syncthreads();
+        if (!par) {
+            const int gg = l % G, q = l / G, r = q % R2, c = q / R2;
+            const int ky = z_row_ky<KY>(g, a20, r);
+            if (ky >= 0) {
+                Cx<T> *out = b.S + c * g.s_comp + (long)ky * g.Xp + kx0 + gg;
+                const long zs = (long)g.P2 * g.Xp;
+#pragma unroll
+                for (int n = 0; n < H; ++n)
+                    if (n < N3) out[n * zs] = f3::csum(v[f3::bitrev<H>(n)], buf[(H + n) * nl + l]);
+            }
+        }
+    }
 }
 
 // Single-layer variant (N3 == 1, P3 == 1): forward y, tensor product at kz = 0 (each octant row a2
@@ -498,6 +618,9 @@ static void init_attributes_t()
         constexpr int LG = decltype(c)::value;
         set_smem((const void *)k_z_conv<T, LG>);
     });
+    if constexpr (sizeof(T) == 4) {
+        f3::lg_for_each<2, 6>([&](auto c) { set_smem((const void *)k_z_conv_r<decltype(c)::value>); });
+    }
     f3::lg_for_each<0, 11>([&](auto c) {
         constexpr int LG = decltype(c)::value;
         set_smem((const void *)k_y_conv<T, LG>);
@@ -566,6 +689,17 @@ DemagPlan demag_plan(const Geom &g)
             p.z_threads = Z::THREADS;
             p.z_smem = Z::SMEM;
         });
+        // FP32 lines of up to 64: the register z convolution
+        p.z_reg = sizeof(T) == 4 && g.lgP3 >= 2 && g.lgP3 <= 6 && 2 * g.N3 <= g.P3;
+        if (p.z_reg) {
+            f3::lg_dispatch<2, 6>(g.lgP3, [&](auto c) {
+                using Z = ZRTile<decltype(c)::value>;
+                p.z_G = Z::G;
+                p.z_KY = Z::KY;
+                p.z_threads = Z::THREADS;
+                p.z_smem = Z::SMEM;
+            });
+        }
     } else {
         int G = pow2_floor(8L * kMaxThreadsYC<T> / (3L * g.P2));
         G = G > 16 ? 16 : G;
@@ -580,7 +714,8 @@ DemagPlan demag_plan(const Geom &g)
         if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > 8L * p.x_threads) p.ok = false;
     }
     if (g.N3 > 1) {
-        if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) || p.z_threads > kMaxThreads<T>)
+        if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) ||
+            p.z_threads > (p.z_reg ? 1024 : kMaxThreads<T>))
             p.ok = false;
     } else if (3L * p.yc_G * g.P2 > 8L * p.yc_threads || p.yc_threads > kMaxThreadsYC<T>) {
         p.ok = false;
@@ -616,10 +751,20 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
             });
             b.mark("demag_y_fwd");
         }
-        f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
-            constexpr int LG = decltype(c)::value;
-            k_z_conv<T, LG><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b);
-        });
+        if constexpr (sizeof(T) == 4) {
+            if (p.z_reg) {
+                f3::lg_dispatch<2, 6>(g.lgP3, [&](auto c) {
+                    constexpr int LG = decltype(c)::value;
+                    k_z_conv_r<LG><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b);
+                });
+            }
+        }
+        if (!p.z_reg) {
+            f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
+                constexpr int LG = decltype(c)::value;
+                k_z_conv<T, LG><<<dim3(g.Xp / p.z_G, div_up(g.H2, p.z_KY)), p.z_threads, p.z_smem, st>>>(g, b);
+            });
+        }
         b.mark("demag_z_conv");
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {

@@ -9,8 +9,10 @@
 // stages go through shared memory.
 //
 // Shared-memory layouts of a block's nl lines:
-//   LF (lines fastest):  element i of line l at buf[i * nl + l]   (consecutive threads take
-//                        consecutive lines, so no padding is needed)
+//   LF (lines fastest):  element i of line l at buf[lfpad(i) * nl + l], lfpad(i) = i + (i >> LFP) with
+//                        one padding row every 2^LFP elements when LFP > 0 (consecutive threads take
+//                        consecutive lines; the padding rows break the strided bank pattern of the first
+//                        stage's stores when a block holds only a few lines)
 //   line-major:          element i of line l at buf[l * LSZ + pad16(i)], LSZ = padded_len(2^LG)
 //                        (one pad slot per 16 elements breaks the strided bank pattern of the early
 //                        stages)
@@ -33,6 +35,10 @@ __host__ __device__ constexpr int stage_slg(int LG, int s, int RM = 3)
 }
 
 __host__ __device__ constexpr int pad16c(int i) { return i + (i >> 4); }
+template <int LFP>
+__host__ __device__ constexpr int lfpad(int i) { return LFP > 0 ? i + (i >> LFP) : i; }
+// rows of the LF layout for lines of L elements
+__host__ __device__ constexpr int lf_rows(int L, int LFP) { return LFP > 0 ? L + (L >> LFP) : L; }
 __host__ __device__ constexpr int padded(int L) { return L + (L >> 4) + 1; }
 
 // cos and sin of 2 pi k / 16 (k mod 16), folded to constants at each call site
@@ -104,7 +110,7 @@ __device__ __forceinline__ Cx<T> cdiff(Cx<T> a, Cx<T> b)
 }
 
 // x_k <- sum_j x_j e^{DIR 2 pi i jk / R}: radix-2 decimation-in-frequency network, X_k in x[bitrev(k)]
-template <typename T, int R, int DIR>
+template <typename T, int R, int DIR, bool PK = true>
 __device__ __forceinline__ void dft(Cx<T> *x)
 {
 #pragma unroll
@@ -114,8 +120,8 @@ __device__ __forceinline__ void dft(Cx<T> *x)
 #pragma unroll
             for (int k = 0; k < h; ++k) {
                 const Cx<T> a = x[s + k], b = x[s + k + h];
-                x[s + k] = csum(a, b);
-                const Cx<T> d = cdiff(a, b);
+                x[s + k] = PK ? csum(a, b) : a + b;
+                const Cx<T> d = PK ? cdiff(a, b) : a - b;
                 const int q = k * (8 / h);  // W_{2h}^k = W_16^q
                 if (q == 0) x[s + k + h] = d;
                 else if (q == 4) x[s + k + h] = mul_si(d, DIR);
@@ -128,6 +134,71 @@ __device__ __forceinline__ void dft(Cx<T> *x)
     }
 }
 
+// cos(2 pi num / den) at compile time: reflection to an angle in [0, pi/4] and a Taylor series there
+// (14 terms: far below double rounding), for the constants of the in-register transforms below
+__host__ __device__ constexpr double taylor_cos(double x)
+{
+    double t = 1.0, s = 1.0;
+    for (int k = 1; k < 14; ++k) {
+        t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double taylor_sin(double x)
+{
+    double t = x, s = x;
+    for (int k = 1; k < 14; ++k) {
+        t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+        s += t;
+    }
+    return s;
+}
+__host__ __device__ constexpr double cos2pi(int num, int den)
+{
+    constexpr double kPi = 3.14159265358979323846;
+    num = ((num % den) + den) % den;
+    if (2 * num > den) num = den - num;  // cos(2 pi f) = cos(2 pi (1 - f)): angle in [0, pi]
+    const double x = 2.0 * kPi * (double)num / (double)den;
+    if (x > 0.5 * kPi) {
+        const double y = kPi - x;  // cos x = -cos(pi - x)
+        return y > 0.25 * kPi ? -taylor_sin(0.5 * kPi - y) : -taylor_cos(y);
+    }
+    return x > 0.25 * kPi ? taylor_sin(0.5 * kPi - x) : taylor_cos(x);
+}
+template <typename T, int N>
+struct CosTab {
+    T v[N];
+};
+template <typename T, int N>
+__host__ __device__ constexpr CosTab<T, N> make_cos_tab()
+{
+    CosTab<T, N> t{};
+    for (int k = 0; k < N; ++k) t.v[k] = (T)cos2pi(k, N);
+    return t;
+}
+// cos(2 pi k / N), k < N, in the working precision (indexed with unrolled constants)
+template <typename T, int N>
+__device__ constexpr CosTab<T, N> kCos = make_cos_tab<T, N>();
+
+// v * e^{DIR 2 pi i k / N} with k a compile-time constant after unrolling
+template <typename T, int N, int DIR>
+__device__ __forceinline__ Cx<T> rot(Cx<T> v, int k)
+{
+    k &= N - 1;
+    if (k == 0) return v;
+    if (4 * k == N) return mul_si(v, DIR);
+    if (4 * k == 3 * N) return mul_si(v, -DIR);
+    if (2 * k == N) return cx<T>(-v.x, -v.y);
+    const T c = kCos<T, N>.v[k], s = DIR > 0 ? kCos<T, N>.v[(k - N / 4) & (N - 1)] : -kCos<T, N>.v[(k - N / 4) & (N - 1)];
+    return cx<T>(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
+// A whole transform of R <= 32 values held by one thread: X_k = sum_j x_j e^{DIR 2 pi i jk / R}, X_k in
+// x[bitrev(k)].  R = 32 splits into one radix-2 decimation-in-frequency level and two 16-point networks.
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_reg(Cx<T> *x);
+
 // v * conj^(DIR>0)(w): the twiddle table holds e^{-2 pi i k / 2^twlg}
 template <typename T, int DIR>
 __device__ __forceinline__ Cx<T> twmul(Cx<T> v, Cx<T> w)
@@ -136,13 +207,33 @@ __device__ __forceinline__ Cx<T> twmul(Cx<T> v, Cx<T> w)
     return cx<T>(v.x * w.x + v.y * w.y, v.y * w.x - v.x * w.y);
 }
 
+// packed additions in the in-register transforms too (measured faster than scalar ones)
+constexpr bool kRegPacked = true;
+template <typename T, int R, int DIR>
+__device__ __forceinline__ void dft_reg(Cx<T> *x)
+{
+    static_assert(R >= 1 && R <= 32 && (R & (R - 1)) == 0, "in-register transforms of 1 to 32 values");
+    if constexpr (R == 32) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const Cx<T> a = x[k], b = x[k + 16];
+            x[k] = kRegPacked ? csum(a, b) : a + b;
+            x[k + 16] = rot<T, 32, DIR>(kRegPacked ? cdiff(a, b) : a - b, k);
+        }
+        dft<T, 16, DIR, kRegPacked>(x);
+        dft<T, 16, DIR, kRegPacked>(x + 16);
+    } else if constexpr (R > 1) {
+        dft<T, R, DIR, kRegPacked>(x);
+    }
+}
+
 // Input / output modes of a stage
 enum { IN_FN = 0, IN_SM = 1 };
 enum { OUT_FN = 0, OUT_SM = 1 };
 
 // One stage S of a length-2^LG transform on nl lines (nb = nl * 2^LG / R butterflies).
 template <typename T, int LG, int S, int DIR, bool LF, int IN, int OUT, bool SYNC_IN, bool SYNC_OUT, int EPT,
-          int NLC, typename Src, typename Dst>
+          int NLC, int LFP, typename Src, typename Dst>
 __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const FastDiv &nlf,
                                       const Cx<T> *__restrict__ tw, int twlg, int nin, int nout, const Src &src,
                                       const Dst &dst)
@@ -175,12 +266,15 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const 
                     v[c][r] = (S > 0 || i < nin) ? src(l, i) : cx<T>(T(0), T(0));
                 }
             } else if (LF) {
-                const Cx<T> *p = buf + j * nl + l;
-                const int step = LR * nl;
+                // element j + r LR: lfpad folds into a constant step when LR is a multiple of 2^LFP
+                constexpr bool fold = LFP == 0 || LR % (1 << (LFP > 0 ? LFP : 0)) == 0;
+                const Cx<T> *p = buf + lfpad<LFP>(j) * nl + l;
+                const int step = lf_rows(LR, LFP) * nl;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const int i = j + r * LR;
-                    v[c][r] = (S > 0 || i < nin) ? p[r * step] : cx<T>(T(0), T(0));
+                    v[c][r] = (S > 0 || i < nin) ? (fold ? p[r * step] : buf[lfpad<LFP>(i) * nl + l])
+                                                 : cx<T>(T(0), T(0));
                 }
             } else {
                 const Cx<T> *p = buf + l * LSZ;
@@ -216,10 +310,14 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const 
                 if (o < nout) dst(l, o, v[c][bitrev<R>(r)]);
             }
         } else if (LF) {
-            Cx<T> *p = buf + d * nl + l;
-            const int step = NS * nl;
+            constexpr bool fold = LFP == 0 || NS % (1 << (LFP > 0 ? LFP : 0)) == 0;
+            Cx<T> *p = buf + lfpad<LFP>(d) * nl + l;
+            const int step = lf_rows(NS, LFP) * nl;
 #pragma unroll
-            for (int r = 0; r < R; ++r) p[r * step] = v[c][bitrev<R>(r)];
+            for (int r = 0; r < R; ++r) {
+                if (fold) p[r * step] = v[c][bitrev<R>(r)];
+                else buf[lfpad<LFP>(d + r * NS) * nl + l] = v[c][bitrev<R>(r)];
+            }
         } else {
             Cx<T> *p = buf + l * LSZ;
             const int pd = pad16c(d);
@@ -233,8 +331,8 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const 
     if (SYNC_OUT) __syncthreads();
 }
 
-template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT, int NLC, typename Src,
-          typename Dst>
+template <typename T, int LG, int S, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT, int NLC, int LFP,
+          typename Src, typename Dst>
 __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw,
                                            int twlg, int nin, int nout, const Src &src, const Dst &dst)
 {
@@ -245,9 +343,9 @@ __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nl
         constexpr int OUT = (last && !DST_SM) ? OUT_FN : OUT_SM;
         constexpr bool SYNC_IN = IN == IN_SM && OUT == OUT_SM;  // in place: all reads before any write
         constexpr bool SYNC_OUT = OUT == OUT_SM;
-        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT, EPT, NLC>(buf, nl, nlf, tw, twlg, first ? nin : (1 << LG),
-                                                                    last ? nout : (1 << LG), src, dst);
-        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM, EPT, NLC>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+        stage<T, LG, S, DIR, LF, IN, OUT, SYNC_IN, SYNC_OUT, EPT, NLC, LFP>(
+            buf, nl, nlf, tw, twlg, first ? nin : (1 << LG), last ? nout : (1 << LG), src, dst);
+        run_stages<T, LG, S + 1, DIR, LF, SRC_SM, DST_SM, EPT, NLC, LFP>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
     }
 }
 
@@ -256,15 +354,16 @@ __device__ __forceinline__ void run_stages(Cx<T> *buf, int nl, const FastDiv &nl
 // otherwise src(l, i) is called for i < nin.  DST_SM: the last stage writes the shared layout
 // (followed by a barrier); otherwise dst(l, o, v) is called for o < nout.
 // EPT (8 or 16) values per thread per stage: needs nl * 2^LG <= EPT * blockDim.x.  NLC > 0: the line
-// count is the compile-time constant NLC (nl and nlf are then ignored).
-template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT = 8, int NLC = 0, typename Src,
-          typename Dst>
+// count is the compile-time constant NLC (nl and nlf are then ignored).  LFP: row padding of the LF layout.
+template <typename T, int LG, int DIR, bool LF, bool SRC_SM, bool DST_SM, int EPT = 8, int NLC = 0, int LFP = 0,
+          typename Src, typename Dst>
 __device__ __forceinline__ void fft(Cx<T> *buf, int nl, const FastDiv &nlf, const Cx<T> *__restrict__ tw, int twlg,
                                     int nin, int nout, const Src &src, const Dst &dst)
 {
     static_assert(LG >= 1, "length-1 transforms are copies");
     static_assert(EPT == 8 || EPT == 16, "8 or 16 values per thread");
-    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM, EPT, NLC>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
+    static_assert(LF || LFP == 0, "row padding belongs to the lines-fastest layout");
+    run_stages<T, LG, 0, DIR, LF, SRC_SM, DST_SM, EPT, NLC, LFP>(buf, nl, nlf, tw, twlg, nin, nout, src, dst);
 }
 
 // placeholder functor for a stage side that is shared memory

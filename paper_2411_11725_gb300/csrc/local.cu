@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 4 : 3) k_node(Lo
                 if (y_next) {
                     // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working
                     // precision
-                    const T as = sizeof(T) == 4 ? (T)sa.af[sa.s - 1] : (T)sa.a[sa.s - 1];
+                    const T as = sizeof(T) == 4 ? (T)sa.af_s : (T)sa.a_s;
                     const T ax = px + as * kx, ay = py + as * ky, az = pz + as * kz;
                     if (sizeof(T) == 4 && sa.mf) {
                         // FP32 path: y_{s+1} is an FP32 quantity, formed from the FP32 copy of m

@@ -49,6 +49,8 @@ struct StageArgs {
     int s;                    // stage index (1-based) of the slope being computed
     double c_s;               // time fraction of stage s
     float af[8];              // the same coefficients in FP32 (used by the FP32 path)
+    double a_s;               // a_{s+1, s}: the coefficient of the slope being written (a[s - 1])
+    float af_s;
     const StepCtl *ctl;       // t, dt
     double t_fixed;           // time when ctl == NULL
 };
