@@ -275,6 +275,134 @@ __device__ __forceinline__ void advance_node(long n, long ns, const double *__re
     }
 }
 
+// FP32 <-> FP64 conversions with integer operations, bit-identical to the hardware conversions in the
+// normal range (float -> double is exact; double -> float rounds to nearest even).  Magnitudes below
+// the smallest normal float (1.2e-38) become signed zeros; out-of-range values take the hardware path.
+// The update of the FP32 path is bound by GB300's FP64 pipe, which would also carry the conversions.
+__device__ __forceinline__ double f2d_int(float x)
+{
+    const unsigned u = __float_as_uint(x), a = u & 0x7fffffffu;
+    if (a < 0x00800000u) return 0.0;
+    if (a >= 0x7f800000u) return (double)x;
+    const unsigned hi = (u & 0x80000000u) | ((a >> 3) + 0x38000000u);  // exponent bias 127 -> 1023
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+__device__ __forceinline__ float d2f_int(double v)
+{
+    const unsigned hi = (unsigned)__double2hiint(v), lo = (unsigned)__double2loint(v);
+    const unsigned ahi = hi & 0x7fffffffu, sign = hi & 0x80000000u, e = ahi >> 20;
+    if (e <= 896u) return __uint_as_float(sign);
+    if (e >= 1151u) return (float)v;
+    unsigned f = ((e - 896u) << 23) | ((ahi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned r = lo & 0x1fffffffu;  // the 29 dropped mantissa bits
+    f += (r > 0x10000000u || (r == 0x10000000u && (f & 1u))) ? 1u : 0u;  // a carry moves into the exponent
+    return __uint_as_float(sign | f);
+}
+
+// v <- m + d (d = dt sum_j b_j k_j in FP32), optionally renormalised, and its FP32 copy.  FP64 work: the
+// three additions, s = |v|^2 (three operations), e = s - 1, and v (1 + rho) with
+//   rho = (1 + e)^(-1/2) - 1 = -e/2 + 3e^2/8 - 5e^3/16 + 35e^4/128 + O(e^5):
+// the first term in FP64, the rest in FP32 (|e| < 1e-3: truncation below 3e-16, |v| - 1 below 1e-13).
+// Larger e (a first step from a state that is not unit length) takes the refined reciprocal square root.
+__device__ __forceinline__ void advance_f32(double v[3], const float d[3], int renorm, float f[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] += f2d_int(d[c]);
+    if (renorm) {
+        const double s = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (s > 0.0) {
+            const double e = s - 1.0;
+            const float ef = d2f_int(e);
+            if (fabsf(ef) < 1e-3f) {
+                const double r = fma(-0.5, e, f2d_int(ef * ef * (0.375f + ef * (-0.3125f + ef * 0.2734375f))));
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = fma(v[c], r, v[c]);
+            } else {
+                const double r = rsqrt_refined(s);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] *= r;
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c] = d2f_int(v[c]);
+}
+
+// Accepted DP5 step of the FP32 path with the FP32 copy of m: four consecutive nodes per thread
+// (16-byte slope loads, two 16-byte FP64 loads per component); the ragged tail node by node.
+__global__ void k_dp5_update_f4(long n_nodes, long ns, double *__restrict__ m, KList kb, const float *__restrict__ k7,
+                                float *__restrict__ k1, const StepCtl *ctl, int renorm, float *__restrict__ mf)
+{
+    const long q = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (!ctl->accepted) return;
+    const float dtf = (float)ctl->dt_used;
+    const long n4 = n_nodes >> 2;
+    if (q < n4) {
+        float d[3][4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float4 sb = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j >= kb.n) break;
+                const float4 kv = reinterpret_cast<const float4 *>((const float *)kb.p[j] + c * ns)[q];
+                const float b = kb.af[j];
+                sb.x += b * kv.x; sb.y += b * kv.y; sb.z += b * kv.z; sb.w += b * kv.w;
+            }
+            d[c][0] = dtf * sb.x; d[c][1] = dtf * sb.y; d[c][2] = dtf * sb.z; d[c][3] = dtf * sb.w;
+        }
+        double v[3][4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 a = reinterpret_cast<const double2 *>(m + c * ns)[2 * q];
+            const double2 b = reinterpret_cast<const double2 *>(m + c * ns)[2 * q + 1];
+            v[c][0] = a.x; v[c][1] = a.y; v[c][2] = b.x; v[c][3] = b.y;
+        }
+        float f[3][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            double w[3] = {v[0][u], v[1][u], v[2][u]};
+            const float dd[3] = {d[0][u], d[1][u], d[2][u]};
+            float ff[3];
+            advance_f32(w, dd, renorm, ff);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c][u] = w[c];
+                f[c][u] = ff[c];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            reinterpret_cast<double2 *>(m + c * ns)[2 * q] = make_double2(v[c][0], v[c][1]);
+            reinterpret_cast<double2 *>(m + c * ns)[2 * q + 1] = make_double2(v[c][2], v[c][3]);
+            reinterpret_cast<float4 *>(mf + c * ns)[q] = make_float4(f[c][0], f[c][1], f[c][2], f[c][3]);
+            reinterpret_cast<float4 *>(k1 + c * ns)[q] = reinterpret_cast<const float4 *>(k7 + c * ns)[q];
+        }
+    }
+    if (q < (n_nodes & 3)) {
+        const long n = 4 * n4 + q;
+        double w[3];
+        float dd[3], ff[3];
+        for (int c = 0; c < 3; ++c) {
+            const long i = c * ns + n;
+            float sb = 0.f;
+            for (int j = 0; j < 8; ++j) {
+                if (j >= kb.n) break;
+                sb += kb.af[j] * ((const float *)kb.p[j])[i];
+            }
+            dd[c] = dtf * sb;
+            w[c] = m[i];
+        }
+        advance_f32(w, dd, renorm, ff);
+        for (int c = 0; c < 3; ++c) {
+            const long i = c * ns + n;
+            m[i] = w[c];
+            mf[i] = ff[c];
+            k1[i] = k7[i];
+        }
+    }
+}
+
 // Accepted step: m <- m5 (optionally renormalised), k1 <- k7 (FSAL).  Rejected: nothing.
 template <typename T>
 __global__ void k_dp5_update(long n_nodes, long ns, double *__restrict__ m, KList kb, const T *__restrict__ k7,
@@ -518,6 +646,14 @@ template <typename T>
 void launch_dp5_update(const Geom &g, double *m, const KList &kb, const T *k7, T *k1, const StepCtl *ctl, int renorm,
                        cudaStream_t st, float *mf)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (mf) {
+            const long n4 = g.n_nodes >> 2;
+            k_dp5_update_f4<<<div_up(n4 > 4 ? n4 : 4, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), (const float *)k7,
+                                                                           (float *)k1, ctl, renorm, mf);
+            return;
+        }
+    }
     k_dp5_update<T><<<div_up(g.n_nodes, 256), 256, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), k7, k1, ctl, renorm, mf);
 }
 
