@@ -441,54 +441,76 @@ __global__ void __launch_bounds__(kMaxThreads<T>, kMinBlocks<T>) k_z_conv(Geom g
     f3::fft<T, LG, +1, true, true, false, Z::EPT, nl>(buf, nl, nlf, b.tw, g.twlg, P3, g.N3, f3::NoFn<T>(), dst);
 }
 
-// Register z convolution (FP32, P3 = 2^LG <= 64).  The z input is zero above N3 <= P3/2, so the
-// spectrum splits by parity: X_{2k+r} = sum_{n<H} (x_n w^{rn}) e^{-2 pi i nk/H}, w = e^{-2 pi i/P3},
-// H = P3/2, and the inverse kept for z < N3 is y_n = u0_n + conj(w)^n u1_n with u_r the inverse
-// length-H transform of the parity-r half.  Each line gets two threads, one per parity, and each
-// thread runs its whole length-H transform in registers: no shared-memory exchanges between FFT
-// stages.  Shared layout: the tile of z_tile_load; after the forward transform, kz = 2k + r of line l
-// sits in row r*H + k.
-template <int LG>
+// Register z convolution (FP32, P3 = 2^LG <= 64).  The z input is zero above N3 <= P3/2, so with
+// S threads per line (S = 2 or 4) and D = P3/S the spectrum splits into S interleaved parts:
+//   X_{Sk+r} = sum_{m<D} e^{-2 pi i mk/D} w^{mr} sum_{j<S/2} w_S^{jr} x_{m+jD},
+// w = e^{-2 pi i/P3}, w_S = w^D, and the inverse kept for z = m + jD < N3 is
+//   y_{m+jD} = sum_r conj(w_S)^{jr} conj(w)^{mr} u_r[m],   u_r = length-D inverse transform of part r.
+// Thread r of a line forms its part and runs the whole length-D transform in registers: no
+// shared-memory exchange between FFT stages.  Shared layout: the tile of z_tile_load; after the forward
+// transform, kz = Sk + r of line l sits in row rD + k; the inverse leaves conj(w)^{mr} u_r[m] in the same
+// rows and the S threads of a line then share the sums over r.
+template <int LG, int S>
 struct ZRTile {
-    static constexpr int P3 = 1 << LG, H = P3 / 2, G = 16;
+    static constexpr int P3 = 1 << LG, D = P3 / S, G = 16;
     static constexpr int KY0 = pow2_floor_c(56 * 1024 / (6 * G * P3 * 8));
     static constexpr int KY = KY0 < 1 ? 1 : (KY0 > 2 ? 2 : KY0);
-    static constexpr int NL = 6 * KY * G;  // lines (a multiple of 32: warps hold one parity)
-    static constexpr int THREADS = 2 * NL;
-    static constexpr size_t SMEM = (size_t)NL * P3 * sizeof(Cx<float>) + (size_t)6 * (H + 1) * KY * G * sizeof(float);
-    static_assert(LG >= 2 && LG <= 6 && NL % 32 == 0 && THREADS <= 1024, "register z tile");
+    static constexpr int NL = 6 * KY * G;  // lines (a multiple of 32: warps hold one part r)
+    static constexpr int THREADS = S * NL;
+    static constexpr size_t SMEM = (size_t)NL * P3 * sizeof(Cx<float>) + (size_t)6 * (P3 / 2 + 1) * KY * G * sizeof(float);
+    static_assert(LG >= 2 && LG <= 6 && (S == 2 || S == 4) && D >= 2 && NL % 32 == 0 && THREADS <= 1024,
+                  "register z tile");
 };
+// threads per line of the register z convolution: 2 (measured on 64-point lines: 1.21 ms against 1.59 ms
+// with 4 threads of 16-point transforms, although those fit twice the resident warps)
+template <int LG>
+constexpr int kZRSplit = 2;
 
 template <int LG>
-__global__ void __launch_bounds__(ZRTile<LG>::THREADS, LG >= 6 ? 3 : 2) k_z_conv_r(Geom g, DemagBufs<float> b)
+__global__ void __launch_bounds__(ZRTile<LG, kZRSplit<LG>>::THREADS, kZRSplit<LG> == 4 ? 3 : (LG >= 6 ? 3 : 2))
+    k_z_conv_r(Geom g, DemagBufs<float> b)
 {
     using T = float;
-    using Z = ZRTile<LG>;
+    constexpr int S = kZRSplit<LG>;
+    using Z = ZRTile<LG, S>;
     if (b.ctl && b.ctl->done) return;
-    constexpr int P3 = Z::P3, H = Z::H, H3 = H + 1, G = Z::G, KY = Z::KY, R2 = 2 * KY, nl = Z::NL;
+    constexpr int P3 = Z::P3, D = Z::D, H = P3 / 2, H3 = H + 1, G = Z::G, KY = Z::KY, R2 = 2 * KY, nl = Z::NL;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
     z_tile_load<T, G, KY, P3>(g, b, buf, kx0, a20);
-    const int par = threadIdx.x >= nl ? 1 : 0, l = threadIdx.x - par * nl;
+    const int r = threadIdx.x / nl, l = threadIdx.x - r * nl;
     const int N3 = g.N3;
     {
-        // forward: parity par of the line's spectrum
-        Cx<T> v[H];
+        // forward: part r of the line's spectrum
+        Cx<T> v[D];
 #pragma unroll
-        for (int n = 0; n < H; ++n) v[n] = n < N3 ? buf[n * nl + l] : cx<T>(T(0), T(0));
-        __syncthreads();  // both parities have read the input rows before either overwrites them
-        if (par) {
-#pragma unroll
-            for (int n = 1; n < H; ++n) v[n] = f3::rot<T, P3, -1>(v[n], n);
+        for (int m = 0; m < D; ++m) {
+            v[m] = m < N3 ? buf[m * nl + l] : cx<T>(T(0), T(0));
+            if (S == 4) {
+                // x_{m+D} w_S^r, w_S = -i (forward)
+                const Cx<T> x1 = m + D < N3 ? buf[(m + D) * nl + l] : cx<T>(T(0), T(0));
+                const Cx<T> t = r == 0 ? x1 : (r == 1 ? mul_si(x1, -1) : (r == 2 ? cx<T>(-x1.x, -x1.y) : mul_si(x1, 1)));
+                v[m] = f3::csum(v[m], t);
+            }
         }
-        f3::dft_reg<T, H, -1>(v);
+        __syncthreads();  // every part has read the input rows before any overwrites them
+        if (r > 0) {
 #pragma unroll
-        for (int k = 0; k < H; ++k) buf[(par * H + k) * nl + l] = v[f3::bitrev<H>(k)];
+            for (int m = 1; m < D; ++m) {
+                // w^{mr}: r is warp-uniform, the twiddle a compile-time constant per branch
+                if (r == 1) v[m] = f3::rot<T, P3, -1>(v[m], m);
+                else if (S == 4 && r == 2) v[m] = f3::rot<T, P3, -1>(v[m], 2 * m);
+                else if (S == 4 && r == 3) v[m] = f3::rot<T, P3, -1>(v[m], 3 * m);
+            }
+        }
+        f3::dft_reg<T, D, -1>(v);
+#pragma unroll
+        for (int k = 0; k < D; ++k) buf[(r * D + k) * nl + l] = v[f3::bitrev<D>(k)];
     }
     __syncthreads();
     {
-        // H^ = N~ M^ at every (kz, row, kx) of the tile; row q holds kz = 2 (q mod H) + q / H
+        // H^ = N~ M^ at every (kz, row, kx) of the tile; row q holds kz = S (q mod D) + q / D
         const T *ten = reinterpret_cast<const T *>(buf + nl * P3);
         constexpr int tstride = H3 * KY * G, npts = KY * G * P3;
         const int h2 = g.P2 >> 1;
@@ -497,7 +519,7 @@ __global__ void __launch_bounds__(ZRTile<LG>::THREADS, LG >= 6 ? 3 : 2) k_z_conv
             const int gg = t % G, qr = t / G, rr = qr % KY, q = qr / KY;
             const int a2 = a20 + rr;
             if (a2 >= g.H2) continue;
-            const int kz = q < H ? 2 * q : 2 * (q - H) + 1;
+            const int kz = S * (q % D) + q / D;
             const int a3 = kz <= H ? kz : P3 - kz;
             const T s3 = kz <= H ? T(1) : T(-1);
             const T *tp = ten + (a3 * KY + rr) * G + gg;
@@ -518,27 +540,42 @@ __global__ void __launch_bounds__(ZRTile<LG>::THREADS, LG >= 6 ? 3 : 2) k_z_conv
     }
     __syncthreads();
     {
-        // inverse: u_par from rows par*H.., twisted by conj(w)^n for the odd parity; the odd threads
-        // leave their part in their own (consumed) rows, the even threads add it and store z < N3
-        Cx<T> v[H];
+        // inverse of part r, twisted by conj(w)^{mr}, back into the part's own (consumed) rows
+        Cx<T> v[D];
 #pragma unroll
-        for (int k = 0; k < H; ++k) v[k] = buf[(par * H + k) * nl + l];
-        f3::dft_reg<T, H, +1>(v);
-        if (par) {
+        for (int k = 0; k < D; ++k) v[k] = buf[(r * D + k) * nl + l];
+        f3::dft_reg<T, D, +1>(v);
 #pragma unroll
-            for (int n = 0; n < H; ++n)
-                if (n < N3) buf[(H + n) * nl + l] = f3::rot<T, P3, +1>(v[f3::bitrev<H>(n)], n);
+        for (int m = 0; m < D; ++m) {
+            Cx<T> u = v[f3::bitrev<D>(m)];
+            if (r == 1) u = f3::rot<T, P3, +1>(u, m);
+            else if (S == 4 && r == 2) u = f3::rot<T, P3, +1>(u, 2 * m);
+            else if (S == 4 && r == 3) u = f3::rot<T, P3, +1>(u, 3 * m);
+            buf[(r * D + m) * nl + l] = u;
         }
         __syncthreads();
-        if (!par) {
-            const int gg = l % G, q = l / G, r = q % R2, c = q / R2;
-            const int ky = z_row_ky<KY>(g, a20, r);
-            if (ky >= 0) {
-                Cx<T> *out = b.S + c * g.s_comp + (long)ky * g.Xp + kx0 + gg;
-                const long zs = (long)g.P2 * g.Xp;
+        // z = r H/S + i, i < H/S (outputs z < H, shared by the S threads): z = m + jD
+        const int gg = l % G, q = l / G, rw = q % R2, c = q / R2;
+        const int ky = z_row_ky<KY>(g, a20, rw);
+        if (ky >= 0) {
+            Cx<T> *out = b.S + c * g.s_comp + (long)ky * g.Xp + kx0 + gg;
+            const long zs = (long)g.P2 * g.Xp;
+            constexpr int ZP = H / S;  // outputs per thread
 #pragma unroll
-                for (int n = 0; n < H; ++n)
-                    if (n < N3) out[n * zs] = f3::csum(v[f3::bitrev<H>(n)], buf[(H + n) * nl + l]);
+            for (int i = 0; i < ZP; ++i) {
+                const int z = r * ZP + i;
+                if (z >= N3) break;
+                const int m = z % D, j = z / D;  // j < S/2
+                Cx<T> y = buf[m * nl + l];
+#pragma unroll
+                for (int rr = 1; rr < S; ++rr) {
+                    const Cx<T> t = buf[(rr * D + m) * nl + l];
+                    // conj(w_S)^{j rr}: (+i)^{j rr} for S = 4, (-1)^{j rr} for S = 2 (j = 0 there)
+                    const int e = (j * rr) & (S - 1);
+                    const Cx<T> tt = S == 2 ? t : (e == 0 ? t : (e == 1 ? mul_si(t, 1) : (e == 2 ? cx<T>(-t.x, -t.y) : mul_si(t, -1))));
+                    y = f3::csum(y, tt);
+                }
+                out[z * zs] = y;
             }
         }
     }
@@ -693,7 +730,7 @@ DemagPlan demag_plan(const Geom &g)
         p.z_reg = sizeof(T) == 4 && g.lgP3 >= 2 && g.lgP3 <= 6 && 2 * g.N3 <= g.P3;
         if (p.z_reg) {
             f3::lg_dispatch<2, 6>(g.lgP3, [&](auto c) {
-                using Z = ZRTile<decltype(c)::value>;
+                using Z = ZRTile<decltype(c)::value, kZRSplit<decltype(c)::value>>;
                 p.z_G = Z::G;
                 p.z_KY = Z::KY;
                 p.z_threads = Z::THREADS;
