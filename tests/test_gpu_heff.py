@@ -33,8 +33,9 @@ def _heff_gpu(nmgb, p, precision, m, terms, t=0.0):
     return h
 
 
+# N3 = 2..32 covers every z transform length up to 64 (P3 = 4, 8, 16, 32, 64), full and ragged
 SHAPES = [(1, 1, 1), (2, 1, 1), (3, 2, 1), (5, 3, 2), (7, 1, 3), (4, 6, 1), (13, 7, 5), (16, 16, 4), (9, 11, 3),
-          (1, 5, 4)]
+          (1, 5, 4), (6, 5, 9), (3, 4, 16), (3, 4, 20), (2, 3, 32)]
 
 
 @pytest.mark.parametrize("precision", [1, 0])
