@@ -197,6 +197,25 @@ int nm_adjoint_run(nm_mesh mesh, int method, double t_end, double rtol, double a
                    long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps,
                    double *grad_h);
 
+/* Continuous adjoint-state gradient (section "Inverse Micromagnetics", Eqs. adjoint_forward,
+ * adjoint_objective and adjoint_system): n_steps classical Runge-Kutta steps of dt = (t_end - t0)/n_steps
+ * from the resident state (t0) to t_end, the final-time loss
+ *   L = sum_{n,j} weight_{n,j} (m_{n,j}(t_end) - target_{n,j})^2,
+ * and then n_steps Runge-Kutta steps of -dt, backwards from t_end to t0, of the system
+ *   dm/dt = f(t, m),  da/dt = -(df/dm)^T a,  du/dt = -(df/dtheta)^T a,
+ *   m(t_end) = m_output,  a(t_end) = dL/dm(t_end),  u(t_end) = 0.
+ * The trajectory is reconstructed by the backward integration, not stored, so the gradients carry the
+ * reconstruction error (which shrinks with the fourth power of dt); nm_adjoint_run is the exact
+ * gradient of the discrete forward map.  weight, target: HOST FP64 nodal vector fields (target may be
+ * NULL = 0).  Outputs (HOST FP64, each may be NULL except loss): loss; grad_m0 = a(t0) (nodal vector
+ * field); grad_Ms = u(t0) for the cell Ms map (cell scalar field); grad_h = u(t0) for the uniform
+ * applied field amplitude (3 values); m0_rec = the reconstructed m(t0) (nodal vector field).  m is
+ * renormalised after each step, forward and backward, as set by nm_set_integrator.  The resident state
+ * ends at t_end.  Synchronises.  Errors: NM_ERR_ARG (n_steps < 1, t_end <= t0, NULL weight or loss),
+ * NM_ERR_STATE (no material or state), NM_ERR_OOM, NM_ERR_CUDA. */
+int nm_adjoint_continuous(nm_mesh mesh, double t_end, long n_steps, const double *weight, const double *target,
+                          double *loss, double *grad_m0, double *grad_Ms, double *grad_h, double *m0_rec);
+
 /* Sizes of the mesh: nodes, cells, padded FFT lengths P1 P2 P3, and the device bytes the mesh holds. */
 int nm_mesh_info(nm_mesh mesh, long *n_nodes, long *n_cells, int P[3], long *device_bytes);
 

@@ -93,6 +93,7 @@ SIGNATURES = [
     ("nm_profile_step", _i, [_vp, _i, _i, _d, _d, _i, _Pd, ctypes.c_char_p, _Pi]),
     ("nm_h_eff_vjp", _i, [_vp, _vp, _vp, _u, _d, _vp, _vp]),
     ("nm_adjoint_run", _i, [_vp, _i, _d, _d, _d, _d, _d, _Pd, _Pd, _i, _l, _Pd, _Pd, _Pd, _Pl, _Pd]),
+    ("nm_adjoint_continuous", _i, [_vp, _d, _l, _Pd, _Pd, _Pd, _Pd, _Pd, _Pd, _Pd]),
     ("nm_footprint_bytes", _l, [_i, _i, _i, _i]),
     ("nm_sync", _i, [_vp]),
     ("nm_server_create", _i, [_l, _i, ctypes.POINTER(_vp)]),
@@ -363,6 +364,21 @@ class Mesh:
         if field_grad:
             return loss.value, gMs, gm0, ns.value, gh
         return loss.value, gMs, gm0, ns.value
+
+    def adjoint_continuous(self, t_end, n_steps, weight, target=None):
+        """Forward RK4 (n_steps) to t_end with the final-time quadratic loss, then the continuous adjoint
+        system integrated backwards.  Returns (loss, dL/dm0 nodal, dL/dMs (N1,N2,N3), dL/dh (3,),
+        reconstructed m(t0) nodal)."""
+        W = _host_f64(weight, self.nodes + (3,))
+        tg = None if target is None else _host_f64(target, self.nodes + (3,))
+        loss = ctypes.c_double()
+        gm0 = np.zeros(self.nodes + (3,))
+        gMs = np.zeros(self.n)
+        gh = np.zeros(3)
+        m0r = np.zeros(self.nodes + (3,))
+        _check(self.lib.nm_adjoint_continuous(self._h, float(t_end), int(n_steps), _pd(W), _pd(tg),
+                                              ctypes.byref(loss), _pd(gm0), _pd(gMs), _pd(gh), _pd(m0r)))
+        return loss.value, gm0, gMs, gh, m0r
 
     def run_until(self, t_end, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0, sample_dt=0.0):
         """Integrate to t_end; returns (samples (k,3) or None, n_accepted, n_rejected)."""

@@ -598,3 +598,210 @@ extern "C" int nm_adjoint_run(nm_mesh M, int method, double t_end, double rtol, 
                : adjoint_run_t<float>(M, method, t_end, rtol, atol, dt0, sample_dt, weight, target, include_initial,
                                       checkpoint_every, loss, grad_Ms, grad_m0, n_steps, grad_h);
 }
+
+// ------------------------------------------------------------------------------------------------
+// Continuous adjoint-state method (section "Inverse Micromagnetics", Eq. adjoint_system).
+//
+// The forward problem is integrated with n classical Runge-Kutta steps from the resident state to T.
+// The system
+//   dm/dt = f(t, m),   da/dt = -(df/dm)^T a,   du/dt = -(df/dtheta)^T a,
+//   m(T) = m_output,   a(T) = dL/dm(T),        u(T) = 0
+// is then integrated backwards with n steps of -dt.  The m stages are the forward stage kernels run
+// with the negative step; they do not depend on a, so each step forms them first and then the a stages:
+//   a_s = a + h sum_j A_sj ka_j,   ka_s = -(df/dm)(y_s)^T a_s,
+// where the transpose product is evaluated on w_s a_s (w_s = -h b_s) so that the Ms and uniform-field
+// accumulators of llg_vjp collect u's increments -h b_s (df/dtheta)^T a_s directly.  m is renormalised
+// after each backward step when the forward steps renormalise.  Unlike the discrete adjoint, m is
+// reconstructed by the backward integration, not read from checkpoints.
+namespace {
+
+template <typename T>
+int continuous_adjoint_t(nm_mesh M, double t_end, long n, const double *weight, const double *target,
+                         double *loss_out, double *grad_m0, double *grad_Ms, double *grad_h, double *m0_rec)
+{
+    const Geom &g = M->g;
+    const size_t nb3 = 3 * g.ns * sizeof(T), nd3 = 3 * g.ns * sizeof(double);
+    int rc = ensure_vjp_buffers<T>(M);
+    if (rc) return rc;
+    const Tableau tb = tableau(NM_RK4);
+    struct MfOff {
+        nm_mesh M;
+        float *mf;
+        explicit MfOff(nm_mesh m) : M(m), mf(m->mf)
+        {
+            M->mf = nullptr;
+            free_graphs(M);
+        }
+        ~MfOff()
+        {
+            M->mf = mf;
+            M->mf_valid = false;
+            free_graphs(M);
+        }
+    } mf_off(M);
+    std::vector<void *> owned;
+    auto galloc = [&](void **p, size_t bytes) -> int {
+        cudaError_t e = cudaMallocAsync(p, bytes, M->st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NM_ERR_OOM, "adjoint workspace allocation failed (%zu bytes)", bytes);
+        }
+        owned.push_back(*p);
+        return NM_OK;
+    };
+    auto release_all = [&]() {
+        M->vj_gh = nullptr;
+        for (void *p : owned) cudaFreeAsync(p, M->st);
+        owned.clear();
+    };
+#define CA_TRY(x)                 \
+    do {                          \
+        int _r = (x);             \
+        if (_r) {                 \
+            release_all();        \
+            return _r;            \
+        }                         \
+    } while (0)
+    AdjBufs<T> A{};
+    for (int s = 0; s < tb.S; ++s) {
+        CA_TRY(galloc((void **)&A.Y[s], nb3));
+        CA_TRY(galloc((void **)&A.YB[s], nb3));  // ka_s
+    }
+    T *C = nullptr, *YB = nullptr;
+    double *a = nullptr, *as = nullptr, *W = nullptr, *tgt = nullptr, *tmp = nullptr, *m_end = nullptr;
+    CA_TRY(galloc((void **)&C, nb3));
+    CA_TRY(galloc((void **)&YB, nb3));
+    CA_TRY(galloc((void **)&a, nd3));
+    CA_TRY(galloc((void **)&as, nd3));
+    CA_TRY(galloc((void **)&m_end, nd3));
+    CA_TRY(galloc((void **)&A.partials, 1024 * sizeof(double)));
+    CA_TRY(galloc((void **)&A.scalar, sizeof(double)));
+    CA_TRY(galloc((void **)&W, nd3));
+    const size_t tmp_bytes = (g.n_nodes * 3 > g.n_cells ? g.n_nodes * 3 : g.n_cells) * sizeof(double);
+    CA_TRY(galloc((void **)&tmp, tmp_bytes));
+    CUDA_TRY(cudaMemcpyAsync(tmp, weight, g.n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, M->st));
+    CUDA_TRY(cudaMemsetAsync(W, 0, nd3, M->st));
+    launch_aos_to_soa<double, double>(g, tmp, W, M->st);
+    if (target) {
+        CA_TRY(galloc((void **)&tgt, nd3));
+        CUDA_TRY(cudaMemcpyAsync(tmp, target, g.n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, M->st));
+        CUDA_TRY(cudaMemsetAsync(tgt, 0, nd3, M->st));
+        launch_aos_to_soa<double, double>(g, tmp, tgt, M->st);
+    }
+    if (grad_h) {
+        double *gh = nullptr;
+        CA_TRY(galloc((void **)&gh, nd3));
+        CUDA_TRY(cudaMemsetAsync(gh, 0, nd3, M->st));
+        M->vj_gh = gh;
+    }
+    CUDA_TRY(cudaMemsetAsync(M->vj_gMs, 0, g.cs * sizeof(double), M->st));
+
+    // forward: n RK4 steps to t_end
+    CA_TRY(pull_ctl(M));
+    const double t0 = M->hctl->t, dt = (t_end - t0) / (double)n;
+    if (!(dt > 0)) {
+        release_all();
+        return fail(NM_ERR_ARG, "need t_end > t");
+    }
+    for (long k = 0; k < n; ++k) {
+        CA_TRY(set_ctl(M, t0 + k * dt, dt));
+        run_stages<T>(M, tb, A);
+        CA_TRY(finish_step<T>(M, tb));
+        CHECK_LAUNCH();
+    }
+    // loss and a(T) = dL/dm(T)
+    CUDA_TRY(cudaMemsetAsync(a, 0, nd3, M->st));
+    CA_TRY(sample_loss<T>(M, W, tgt, a, A, loss_out));
+    CUDA_TRY(cudaMemcpyAsync(m_end, M->m, nd3, cudaMemcpyDeviceToDevice, M->st));
+
+    // backward: n steps of -dt for (m, a, u)
+    const double hb = -dt;
+    for (long k = 0; k < n; ++k) {
+        const double t = t_end - k * dt;
+        CA_TRY(set_ctl(M, t, hb));
+        run_stages<T>(M, tb, A);  // y_s in A.Y, f(y_s) in M->k
+        for (int s = 1; s <= tb.S; ++s) {
+            LinComb lc{};
+            lc.pd[0] = a;
+            lc.ad[0] = 1.0;
+            lc.nd = 1;
+            for (int j = 1; j < s; ++j)
+                if (tb.a[s - 1][j - 1] != 0.0) {
+                    lc.pt[lc.nt] = A.YB[j - 1];
+                    lc.at[lc.nt++] = hb * tb.a[s - 1][j - 1];
+                }
+            launch_lincomb_d<T>(g, lc, as, M->st);
+            const double w = -hb * tb.b[s - 1];
+            LinComb sc{};
+            sc.pd[0] = as;
+            sc.ad[0] = w;
+            sc.nd = 1;
+            launch_lincomb<T>(g, sc, C, M->st);
+            llg_vjp<T>(M, A.Y[s - 1], t + tb.c[s - 1] * hb, C, YB);
+            launch_axpby<T>(g, T(-1.0 / w), YB, T(0), YB, A.YB[s - 1], M->st);
+        }
+        CA_TRY(finish_step<T>(M, tb));  // m <- N(m + h sum b_s f(y_s))
+        LinComb lc{};
+        lc.pd[0] = a;
+        lc.ad[0] = 1.0;
+        lc.nd = 1;
+        for (int s = 1; s <= tb.S; ++s) {
+            lc.pt[lc.nt] = A.YB[s - 1];
+            lc.at[lc.nt++] = hb * tb.b[s - 1];
+        }
+        launch_lincomb_d<T>(g, lc, as, M->st);
+        CUDA_TRY(cudaMemcpyAsync(a, as, nd3, cudaMemcpyDeviceToDevice, M->st));
+        CHECK_LAUNCH();
+    }
+    // outputs
+    if (grad_m0) {
+        launch_soa_to_aos<double, double>(g, a, tmp, M->st);
+        CUDA_TRY(cudaMemcpyAsync(grad_m0, tmp, g.n_nodes * 3 * sizeof(double), cudaMemcpyDeviceToHost, M->st));
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+    }
+    if (m0_rec) {
+        launch_soa_to_aos<double, double>(g, M->m, tmp, M->st);
+        CUDA_TRY(cudaMemcpyAsync(m0_rec, tmp, g.n_nodes * 3 * sizeof(double), cudaMemcpyDeviceToHost, M->st));
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+    }
+    if (grad_Ms) {
+        launch_cells_to_boundary<double>(g, M->vj_gMs, tmp, M->st);
+        CUDA_TRY(cudaMemcpyAsync(grad_Ms, tmp, g.n_cells * sizeof(double), cudaMemcpyDeviceToHost, M->st));
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+    }
+    if (grad_h) {
+        launch_sum_nodal3(g, M->vj_gh, M->partials, M->mean_d, M->st);
+        CHECK_LAUNCH();
+        CUDA_TRY(cudaMemcpyAsync(M->mean_h, M->mean_d, 3 * sizeof(double), cudaMemcpyDeviceToHost, M->st));
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+        for (int c = 0; c < 3; ++c) grad_h[c] = M->mean_h[c];
+    }
+    // leave the resident state at the end of the forward run
+    CUDA_TRY(cudaMemcpyAsync(M->m, m_end, nd3, cudaMemcpyDeviceToDevice, M->st));
+    CA_TRY(set_ctl(M, t_end, dt));
+    M->k1_valid = false;
+    CHECK_LAUNCH();
+    CUDA_TRY(cudaStreamSynchronize(M->st));
+    release_all();
+    CUDA_TRY(cudaStreamSynchronize(M->st));
+    return NM_OK;
+#undef CA_TRY
+}
+
+}  // namespace
+
+extern "C" int nm_adjoint_continuous(nm_mesh M, double t_end, long n_steps, const double *weight,
+                                     const double *target, double *loss, double *grad_m0, double *grad_Ms,
+                                     double *grad_h, double *m0_rec)
+{
+    if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
+    if (!M->material_set) return fail(NM_ERR_STATE, "material not set");
+    if (!M->state_set) return fail(NM_ERR_STATE, "no resident state");
+    if (!weight || !loss) return fail(NM_ERR_ARG, "weight and loss are required");
+    if (!isfinite(t_end)) return fail(NM_ERR_ARG, "non-finite argument");
+    if (n_steps < 1) return fail(NM_ERR_ARG, "n_steps must be >= 1");
+    return M->prec == NM_F64 ? continuous_adjoint_t<double>(M, t_end, n_steps, weight, target, loss, grad_m0, grad_Ms,
+                                                            grad_h, m0_rec)
+                             : continuous_adjoint_t<float>(M, t_end, n_steps, weight, target, loss, grad_m0, grad_Ms,
+                                                           grad_h, m0_rec);
+}

@@ -355,7 +355,7 @@ __device__ __forceinline__ int z_row_ky(const Geom &g, int a20, int r)
 // Stage a z tile in shared memory with cp.async: the N3 spectrum rows of its 3 x 2KY lines of G kx
 // columns (element z of line l = (c * 2KY + r) * G + g at buf[z * nl + l]), then the tensor slice
 // [component][a3][row][kx] behind the NL * P3 spectrum values; ends with a barrier.
-template <typename T, int G, int KY, int P3>
+template <typename T, int G, int KY, int P3, bool TENSOR = true>
 __device__ __forceinline__ void z_tile_load(const Geom &g, const DemagBufs<T> &b, Cx<T> *buf, int kx0, int a20)
 {
     constexpr int R2 = 2 * KY, nl = 3 * R2 * G, H3 = P3 / 2 + 1;
@@ -374,7 +374,7 @@ __device__ __forceinline__ void z_tile_load(const Geom &g, const DemagBufs<T> &b
     T *ten = reinterpret_cast<T *>(buf + nl * P3);
     constexpr int trowb = G * (int)sizeof(T);
     constexpr int tcb = trowb >= 16 ? 16 : trowb, tch = trowb / tcb;
-    for (int t = threadIdx.x; t < 6 * H3 * KY * tch; t += blockDim.x) {
+    for (int t = threadIdx.x; TENSOR && t < 6 * H3 * KY * tch; t += blockDim.x) {
         const int row = t / tch, ch = t - row * tch;
         const int rr = row % KY, kq = row / KY, a3 = kq % H3, comp = kq / H3;
         const int a2 = a20 + rr;
@@ -457,7 +457,11 @@ struct ZRTile {
     static constexpr int KY = KY0 < 1 ? 1 : (KY0 > 2 ? 2 : KY0);
     static constexpr int NL = 6 * KY * G;  // lines (a multiple of 32: warps hold one part r)
     static constexpr int THREADS = S * NL;
-    static constexpr size_t SMEM = (size_t)NL * P3 * sizeof(Cx<float>) + (size_t)6 * (P3 / 2 + 1) * KY * G * sizeof(float);
+    // the tensor slice goes through shared memory, except for 64-point lines: there the product reads it
+    // from global memory (L2), so that four blocks fit an SM
+    static constexpr bool TSM = LG < 6;
+    static constexpr size_t SMEM =
+        (size_t)NL * P3 * sizeof(Cx<float>) + (TSM ? (size_t)6 * (P3 / 2 + 1) * KY * G * sizeof(float) : 0);
     static_assert(LG >= 2 && LG <= 6 && (S == 2 || S == 4) && D >= 2 && NL % 32 == 0 && THREADS <= 1024,
                   "register z tile");
 };
@@ -467,7 +471,7 @@ template <int LG>
 constexpr int kZRSplit = 2;
 
 template <int LG>
-__global__ void __launch_bounds__(ZRTile<LG, kZRSplit<LG>>::THREADS, kZRSplit<LG> == 4 ? 3 : (LG >= 6 ? 3 : 2))
+__global__ void __launch_bounds__(ZRTile<LG, kZRSplit<LG>>::THREADS, kZRSplit<LG> == 4 ? 3 : (LG >= 6 ? 4 : 2))
     k_z_conv_r(Geom g, DemagBufs<float> b)
 {
     using T = float;
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(ZRTile<LG, kZRSplit<LG>>::THREADS, kZRSplit<LG
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     const int kx0 = blockIdx.x * G, a20 = blockIdx.y * KY;
-    z_tile_load<T, G, KY, P3>(g, b, buf, kx0, a20);
+    z_tile_load<T, G, KY, P3, Z::TSM>(g, b, buf, kx0, a20);
     const int r = threadIdx.x / nl, l = threadIdx.x - r * nl;
     const int N3 = g.N3;
     {
@@ -522,14 +526,25 @@ __global__ void __launch_bounds__(ZRTile<LG, kZRSplit<LG>>::THREADS, kZRSplit<LG
             const int kz = S * (q % D) + q / D;
             const int a3 = kz <= H ? kz : P3 - kz;
             const T s3 = kz <= H ? T(1) : T(-1);
-            const T *tp = ten + (a3 * KY + rr) * G + gg;
             Ten6<T> tt;
-            tt.xx = tp[0];
-            tt.yy = tp[tstride];
-            tt.zz = tp[2 * tstride];
-            tt.xy = tp[3 * tstride];
-            tt.xz = tp[4 * tstride] * s3;
-            tt.yz = tp[5 * tstride] * s3;
+            if (Z::TSM) {
+                const T *tp = ten + (a3 * KY + rr) * G + gg;
+                tt.xx = tp[0];
+                tt.yy = tp[tstride];
+                tt.zz = tp[2 * tstride];
+                tt.xy = tp[3 * tstride];
+                tt.xz = tp[4 * tstride] * s3;
+                tt.yz = tp[5 * tstride] * s3;
+            } else {
+                const T *tp = b.Nk + ((long)a3 * g.H2 + a2) * g.Xp + kx0 + gg;
+                const long tc = g.t_comp;
+                tt.xx = __ldg(tp);
+                tt.yy = __ldg(tp + tc);
+                tt.zz = __ldg(tp + 2 * tc);
+                tt.xy = __ldg(tp + 3 * tc);
+                tt.xz = __ldg(tp + 4 * tc) * s3;
+                tt.yz = __ldg(tp + 5 * tc) * s3;
+            }
             Cx<T> *p = buf + q * nl + rr * G + gg;
             tensor_mul(tt, T(1), p, p + R2 * G, p + 2 * R2 * G);
             if (a2 > 0 && a2 < h2) {
