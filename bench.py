@@ -403,6 +403,18 @@ def run_ours(args, rank, world, dist):
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(args.serve_requests, int(args.serve_budget_gb * (1 << 30)), args.serve_max_active)
+    film = None
+    if args.film_steps > 0 and rank == 0:
+        try:
+            film = run_film(nmgb, args.film_steps)
+        except Exception as e:  # a side measurement: report it, keep the headline line
+            film = {"error": f"{type(e).__name__}: {e}"}
+    gradients = None
+    if args.grad_steps > 0 and rank == 0:
+        try:
+            gradients = run_gradients(nmgb, args.grad_steps)
+        except Exception as e:  # a side measurement: report it, keep the headline line
+            gradients = {"error": f"{type(e).__name__}: {e}"}
     cpu_v, cores, cs_desc = None, None, "skipped (--cpu-seconds 0)"
     if args.cpu_seconds > 0:
         cpu_v, cores, cs_steps, cs_el, cs_desc = oracle_sample(seconds=args.cpu_seconds)
@@ -431,10 +443,90 @@ def run_ours(args, rank, world, dist):
         "kernels": kernels,
         "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": cs_desc},
         "serving": serving,
+        "gradients": gradients,
+        "thin_film_2d_basis": film,
         "clocks": clocks,
         "gpu_launches": int(launches_per_step * K),
     }
     print(json.dumps(line), flush=True)
+
+
+def run_film(nmgb, n_steps, grid=(1024, 1024, 1)):
+    """A single-layer film (3 nm cells of the throughput material, 1 nm thick), FP32 DP5(4) steps with
+    the trilinear basis (2 node layers) and with the 2D basis (1 node layer, section "Low-Dimensional
+    Geometries"): wall time per step (graph replays, synchronised) and node-steps/s of each."""
+    p = inp.throughput(grid, seed=5, with_m0=False)
+    dx = (p.dx[0], p.dx[1], 1e-9)
+    rng = np.random.default_rng(5)
+    out = {"workload": f"film {grid[0]}x{grid[1]}x{grid[2]} cells of 3x3x1 nm, throughput material, FP32 "
+                       f"field, DP5(4) rtol=atol=1e-5, random unit m0, {n_steps} timed steps"}
+    for basis in (3, 2):
+        me = nmgb.Mesh(p.n, dx, nmgb.F32, basis=basis)
+        me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+        me.set_terms(p.terms)
+        m0 = inp.unit_vectors(rng, me.nodes)
+        me.set_state(m0, 0.0, 1e-15)
+        me.run_steps(3, nmgb.DP54, 1e-5, 1e-5)  # warm-up
+        me.sync()
+        a0, r0, _ = me.counters()
+        t0 = time.perf_counter()
+        me.run_steps(n_steps, nmgb.DP54, 1e-5, 1e-5)
+        me.sync()
+        ms = (time.perf_counter() - t0) * 1e3
+        a1, r1, _ = me.counters()
+        nn = int(np.prod(me.nodes))
+        out[f"basis{basis}"] = {"nodes": nn, "ms_per_step": ms / max(1, (a1 - a0) + (r1 - r0)),
+                                "node_steps_per_s": nn * (a1 - a0) / (ms * 1e-3)}
+        me.close()
+    out["step_time_ratio_3d_over_2d"] = out["basis3"]["ms_per_step"] / out["basis2"]["ms_per_step"]
+    return out
+
+
+def run_gradients(nmgb, n_steps, grid=(256, 256, 8), dt=1e-14):
+    """Wall time of the two gradient methods against the forward integration they differentiate (FP32
+    field, the throughput material): n RK4 steps forward; the discrete adjoint (nm_adjoint_run,
+    checkpointed, exact gradient of the discrete map); the continuous adjoint (nm_adjoint_continuous,
+    backward integration of Eq. adjoint_system).  Also the relative L2 gap between their Ms gradients."""
+    p = inp.throughput(grid, seed=7, with_m0=False)
+    rng = np.random.default_rng(7)
+    m0 = inp.unit_vectors(rng, p.nodes)
+    Wt = rng.uniform(0.5, 1.5, p.nodes + (3,))
+    tgt = inp.unit_vectors(rng, p.nodes)
+    T = n_steps * dt
+
+    def mesh():
+        me = nmgb.Mesh(p.n, p.dx, nmgb.F32)
+        me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+        me.set_terms(p.terms)
+        me.set_state(m0, 0.0, dt)
+        return me
+
+    out = {"workload": f"cuboid {grid[0]}x{grid[1]}x{grid[2]} cells, throughput material, FP32 field, "
+                       f"{n_steps} RK4 steps of {dt:g} s, final-time quadratic loss", "unit": "ms"}
+    me = mesh()
+    me.run_steps(n_steps, nmgb.RK4, 0.0, 0.0)  # warm-up (graphs, workspaces)
+    me.set_state(m0, 0.0, dt)
+    me.sync()
+    t0 = time.perf_counter()
+    me.run_steps(n_steps, nmgb.RK4, 0.0, 0.0)
+    me.sync()
+    out["forward_ms"] = (time.perf_counter() - t0) * 1e3
+    me.set_state(m0, 0.0, dt)
+    me.adjoint_run(T, Wt, tgt, method=nmgb.RK4, dt0=dt)  # warm-up
+    me.set_state(m0, 0.0, dt)
+    t0 = time.perf_counter()
+    _, gd, _, _ = me.adjoint_run(T, Wt, tgt, method=nmgb.RK4, dt0=dt)
+    out["discrete_adjoint_ms"] = (time.perf_counter() - t0) * 1e3
+    me.set_state(m0, 0.0, dt)
+    me.adjoint_continuous(T, n_steps, Wt, tgt)  # warm-up
+    me.set_state(m0, 0.0, dt)
+    t0 = time.perf_counter()
+    _, _, gc, _, m0r = me.adjoint_continuous(T, n_steps, Wt, tgt)
+    out["continuous_adjoint_ms"] = (time.perf_counter() - t0) * 1e3
+    me.close()
+    out["ms_gradient_rel_l2_gap"] = float(np.linalg.norm(gc - gd) / np.linalg.norm(gd))
+    out["m0_reconstruction_max_err"] = float(np.abs(m0r - m0).max())
+    return out
 
 
 def serving_kwargs(i, p):
@@ -510,6 +602,8 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=40, help="requests per serving load level (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-active", type=int, default=16)
+    ap.add_argument("--grad-steps", type=int, default=16, help="RK4 steps of the gradient timing leg (0: skip)")
+    ap.add_argument("--film-steps", type=int, default=10, help="DP5 steps of the 2D-basis film leg (0: skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -81,6 +81,16 @@ typedef struct nm_mesh_s *nm_mesh;
 int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision,
                    void *cuda_stream, nm_mesh *out);
 
+/* As nm_create_mesh, with the nodal basis chosen (section "Low-Dimensional Geometries"): basis 3 is the
+ * trilinear basis of nm_create_mesh, (n1+1) x (n2+1) x (n3+1) nodes; basis 2 is the 2D nodal basis with
+ * full 3D integration, (n1+1) x (n2+1) x 1 nodes whose basis functions are constant along z over all n3
+ * cell layers (thin films: half the degrees of freedom of one cell layer).  Every nodal field of a
+ * basis-2 mesh has shape (n1+1, n2+1, 1, 3); cell fields keep all n3 layers.  The transpose product and
+ * both adjoints (nm_h_eff_vjp, nm_adjoint_run, nm_adjoint_continuous) need basis 3 and return
+ * NM_ERR_ARG on a basis-2 mesh.  Errors: as nm_create_mesh; NM_ERR_ARG for a basis other than 2 or 3. */
+int nm_create_mesh_basis(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, int basis,
+                         void *cuda_stream, nm_mesh *out);
+
 /* Release a mesh and all its device memory (synchronises its stream).  NULL is accepted. */
 int nm_destroy_mesh(nm_mesh mesh);
 

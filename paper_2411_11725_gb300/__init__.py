@@ -75,6 +75,7 @@ class ServerStats(ctypes.Structure):
 
 SIGNATURES = [
     ("nm_create_mesh", _i, [_i, _i, _i, _d, _d, _d, _i, _vp, ctypes.POINTER(_vp)]),
+    ("nm_create_mesh_basis", _i, [_i, _i, _i, _d, _d, _d, _i, _i, _vp, ctypes.POINTER(_vp)]),
     ("nm_destroy_mesh", _i, [_vp]),
     ("nm_set_material", _i, [_vp, _Pd, _d, _Pd, _d, _Pd, _d, _Pd, _d, _d]),
     ("nm_set_field", _i, [_vp, _i, _Pd, _Pd, _d, _d]),
@@ -154,7 +155,9 @@ class Mesh:
     (default: the library creates its own stream).
     """
 
-    def __init__(self, n, dx, precision=F32, stream=None):
+    def __init__(self, n, dx, precision=F32, stream=None, basis=3):
+        """basis 3: trilinear nodal basis; basis 2: nodal basis constant along z over all cell layers
+        (nodes (N1+1, N2+1, 1), section "Low-Dimensional Geometries")."""
         import torch
         if not torch.cuda.is_available():
             raise NMError(ERR_CUDA, "no CUDA device: this library has no CPU path")
@@ -163,13 +166,17 @@ class Mesh:
         self.n = tuple(int(v) for v in n)
         self.dx = tuple(float(v) for v in dx)
         self.precision = int(precision)
-        self.nodes = tuple(v + 1 for v in self.n)
+        self.basis = int(basis)
+        self.nodes = (self.n[0] + 1, self.n[1] + 1, 1 if self.basis == 2 else self.n[2] + 1)
         self.dtype = torch.float64 if self.precision == F64 else torch.float32
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream
         sp = None if stream is None else ctypes.c_void_p(stream.cuda_stream)
         h = ctypes.c_void_p()
-        _check(self.lib.nm_create_mesh(*self.n, *self.dx, self.precision, sp, ctypes.byref(h)))
+        if self.basis == 3:
+            _check(self.lib.nm_create_mesh(*self.n, *self.dx, self.precision, sp, ctypes.byref(h)))
+        else:
+            _check(self.lib.nm_create_mesh_basis(*self.n, *self.dx, self.precision, self.basis, sp, ctypes.byref(h)))
         self._h = h
 
     def close(self):

@@ -38,11 +38,13 @@ static int ilog2i(int v)
     return l;
 }
 
-static Geom make_geom(int n1, int n2, int n3)
+static Geom make_geom(int n1, int n2, int n3, int basis = 3)
 {
     Geom g{};
     g.N1 = n1; g.N2 = n2; g.N3 = n3;
-    g.nn1 = n1 + 1; g.nn2 = n2 + 1; g.nn3 = n3 + 1;
+    g.basis = basis;
+    g.nn1 = n1 + 1; g.nn2 = n2 + 1; g.nn3 = basis == 2 ? 1 : n3 + 1;
+    g.zsn = basis == 2 ? 0 : g.nn1 * g.nn2;
     g.n_nodes = (long)g.nn1 * g.nn2 * g.nn3;
     g.n_cells = (long)n1 * n2 * n3;
     g.ns = round_up(g.n_nodes, 64);
@@ -176,8 +178,19 @@ extern "C" int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, do
     return create_mesh(n1, n2, n3, dx1, dx2, dx3, precision, cuda_stream, nullptr, out);
 }
 
+extern "C" int nm_create_mesh_basis(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision,
+                                    int basis, void *cuda_stream, nm_mesh *out)
+{
+    g_last_error.clear();
+    if (basis != 2 && basis != 3) {
+        if (out) *out = nullptr;
+        return fail(NM_ERR_ARG, "basis must be 3 (trilinear) or 2 (constant along z), got %d", basis);
+    }
+    return create_mesh(n1, n2, n3, dx1, dx2, dx3, precision, cuda_stream, nullptr, out, basis);
+}
+
 int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, void *cuda_stream,
-                nm_mesh tensor_src, nm_mesh *out)
+                nm_mesh tensor_src, nm_mesh *out, int basis)
 {
     if (!out) return fail(NM_ERR_ARG, "out is NULL");
     *out = nullptr;
@@ -196,7 +209,7 @@ int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int 
     nm_mesh M = new nm_mesh_s();
     M->prec = precision;
     M->rs = precision == NM_F64 ? 8 : 4;
-    M->g = make_geom(n1, n2, n3);
+    M->g = make_geom(n1, n2, n3, basis);
     M->dx[0] = dx1; M->dx[1] = dx2; M->dx[2] = dx3;
     if (cuda_stream) {
         M->st = (cudaStream_t)cuda_stream;

@@ -9,7 +9,10 @@ namespace nm {
 
 struct Geom {
     int N1, N2, N3;            // cells
-    int nn1, nn2, nn3;         // nodes = cells + 1
+    int nn1, nn2, nn3;         // nodes = cells + 1 (nn3 = 1 with the 2D basis)
+    int basis;                 // 3: trilinear nodal basis; 2: 2D nodal basis, constant along z over all N3
+                               // cell layers (section "Low-Dimensional Geometries")
+    int zsn;                   // node offset between the z corners of a cell: nn1 nn2 (3D) or 0 (2D)
     long n_nodes, n_cells;
     long ns;                   // component stride of nodal SoA arrays
     long cs;                   // component stride of cell SoA arrays

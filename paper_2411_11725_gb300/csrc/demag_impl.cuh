@@ -115,13 +115,14 @@ __device__ __forceinline__ XInfo x_info(const Geom &g, const FastDiv &nrf, int L
     const int yy = row - zz * g.N2;
     XInfo x;
     x.cell = row * g.N1;
-    x.in = cell_in ? c * (int)g.cs + x.cell : c * (int)g.ns + (zz * g.nn2 + yy) * g.nn1;
+    x.in = cell_in ? c * (int)g.cs + x.cell : c * (int)g.ns + zz * g.zsn + yy * g.nn1;
     x.spec = c * (int)g.s_comp + (zz * g.P2 + yy) * g.Xp;
     return x;
 }
 
 // M of the cell pair (x, x+1) of a row: M_c = Ms_c * (1/8) sum_{i in {0,1}^3} y_{c+i}.  p points at node
-// (x, yy, zz) of one component.
+// (x, yy, zz) of one component; `plane` is the node offset of the upper z corners (0 with the 2D basis,
+// where the 8-corner mean is the mean of the 4 in-plane corners).
 template <typename T>
 __device__ __forceinline__ Cx<T> cell_M_pair(const T *__restrict__ p, int nn1, int plane, const T *__restrict__ Ms,
                                              T Ms0, int cell, bool has2)
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 4 : 2)
     if (nl <= 0) return;
     if (threadIdx.x < nl) info[threadIdx.x] = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), l0 + threadIdx.x, CELL_IN);
     __syncthreads();
-    const int N1 = g.N1, nn1 = g.nn1, plane = g.nn2 * g.nn1;
+    const int N1 = g.N1, nn1 = g.nn1, plane = g.zsn;  // 2D basis: both z corners are the node itself
     const T *Ms = b.Ms;
     const T Ms0 = b.Ms0;
     auto src = [&](int l, int i) -> Cx<T> {
@@ -208,7 +209,7 @@ __global__ void k_x_fwd1(Geom g, DemagBufs<T> b, const T *__restrict__ in)
     const XInfo xi = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), L, CELL_IN);
     T v;
     if (CELL_IN) v = in[xi.in];
-    else v = cell_M_pair<T>(in + xi.in, g.nn1, g.nn2 * g.nn1, b.Ms, b.Ms0, xi.cell, false).x;
+    else v = cell_M_pair<T>(in + xi.in, g.nn1, g.zsn, b.Ms, b.Ms0, xi.cell, false).x;
     b.S[xi.spec] = cx<T>(v, T(0));
 }
 

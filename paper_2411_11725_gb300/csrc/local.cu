@@ -412,6 +412,150 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 4 : 3) k_node(Lo
     }
 }
 
+// 2D basis (section "Low-Dimensional Geometries"): one node layer; the basis function of node (n1, n2)
+// is constant along z over all N3 cell layers, so it couples to the 9 nodes n + o (o in {-1,0,1}^2)
+// through the in-plane cells holding both nodes, in every layer.  With per-layer pattern integrals
+// Wex2, Wm2 (d = 2|o1| + |o2|) the variation at n is
+//   dE_ex = sum_o Wex2[d] (sum_{cells} A_c) (m_{n+o} - m_n),  dE_an = -2 e sum_o Wm2[d] (sum Ku_c) (e . m_{n+o})
+// and the cell->node average takes Ms_c H_c over the 4 in-plane cells of every layer with weight
+// mu0 V/4.  One thread per node; neighbours and cells are read through L1 (thin films: N3 is small).
+template <typename T, bool STAGE>
+__global__ void __launch_bounds__(256) k_node2d(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ out,
+                                                T *__restrict__ y_next, StageArgs sa, double t_heff)
+{
+    if (STAGE && sa.ctl && sa.ctl->done) return;
+    const Geom &g = p.g;
+    const int n1 = blockIdx.x * 32 + (threadIdx.x & 31), n2 = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (n1 >= g.nn1 || n2 >= g.nn2) return;
+    const int ns = (int)g.ns, n = n2 * g.nn1 + n1;
+    const double t = STAGE ? (sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed) : t_heff;
+    const T im = p.inv_mass[n];
+    const bool magnetic = im > T(0);
+    // per in-plane cell (i1, i2): layer sums of A, Ku over magnetic cells, of Ms_c H_c and of Ms_c h_c
+    T SA[4], SK[4];
+    T cx = 0, cy = 0, cz = 0, zx = 0, zy = 0, zz = 0;
+    const bool demag = p.MsH && (p.terms & NM_DEMAG), zee_c = p.Msh && (p.terms & NM_ZEE);
+    const long cs = g.cs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        SA[i] = T(0);
+        SK[i] = T(0);
+        const int c1 = n1 - ((i >> 1) & 1), c2 = n2 - (i & 1);
+        if (c1 < 0 || c1 >= g.N1 || c2 < 0 || c2 >= g.N2) continue;
+        for (int c3 = 0; c3 < g.N3; ++c3) {
+            const int c = (c3 * g.N2 + c2) * g.N1 + c1;
+            const T Ms = p.Ms ? p.Ms[c] : p.Ms0;
+            if (!(Ms > T(0))) continue;
+            if (p.terms & NM_EXCH) SA[i] += p.A ? p.A[c] : p.A0;
+            if (p.terms & NM_ANIS) SK[i] += p.Ku ? p.Ku[c] : p.Ku0;
+            if (demag) {
+                cx += p.MsH[c];
+                cy += p.MsH[cs + c];
+                cz += p.MsH[2 * cs + c];
+            }
+            if (zee_c) {
+                zx += p.Msh[c];
+                zy += p.Msh[cs + c];
+                zz += p.Msh[2 * cs + c];
+            }
+        }
+    }
+    const T mx = y[n], my = y[ns + n], mz = y[2 * ns + n];
+    T ex = 0, ey = 0, ez = 0, pe = 0;
+#pragma unroll
+    for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+        for (int o1 = -1; o1 <= 1; ++o1) {
+            // in-plane cells holding both n and n + o: i_k = 1 where o_k = -1, 0 where o_k = +1, either at 0
+            T S = 0, K = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int i1 = (i >> 1) & 1, i2 = i & 1;
+                if ((o1 == -1 && i1 != 1) || (o1 == 1 && i1 != 0) || (o2 == -1 && i2 != 1) || (o2 == 1 && i2 != 0))
+                    continue;
+                S += SA[i];
+                K += SK[i];
+            }
+            const int d = 2 * (o1 != 0) + (o2 != 0);
+            const int q1 = n1 + o1, q2 = n2 + o2;
+            if (q1 < 0 || q1 >= g.nn1 || q2 < 0 || q2 >= g.nn2) continue;  // (its weights are zero)
+            const int q = q2 * g.nn1 + q1;
+            const T qx = y[q], qy = y[ns + q], qz = y[2 * ns + q];
+            if (o1 != 0 || o2 != 0) {
+                const T w = p.Wex2[d] * S;
+                ex += w * (qx - mx);
+                ey += w * (qy - my);
+                ez += w * (qz - mz);
+            }
+            pe += p.Wm2[d] * K * (p.e0 * qx + p.e1 * qy + p.e2 * qz);
+        }
+    T hx = -ex + T(2) * p.e0 * pe, hy = -ey + T(2) * p.e1 * pe, hz = -ez + T(2) * p.e2 * pe;
+    if (zee_c) {
+        const T sc = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
+        cx += sc * zx;
+        cy += sc * zy;
+        cz += sc * zz;
+    }
+    if (p.raw) {
+        hx += p.mu0V4 * cx;
+        hy += p.mu0V4 * cy;
+        hz += p.mu0V4 * cz;
+    } else {
+        hx = im * (hx + p.mu0V4 * cx);
+        hy = im * (hy + p.mu0V4 * cy);
+        hz = im * (hz + p.mu0V4 * cz);
+        if (magnetic && (p.terms & NM_ZEE)) {
+            const T su = (T)time_factor<T>(p.hu_freq, p.hu_phase, t);
+            hx += (T)p.hu0 * su;
+            hy += (T)p.hu1 * su;
+            hz += (T)p.hu2 * su;
+        }
+    }
+    if (!STAGE) {
+        out[n] = hx;
+        out[ns + n] = hy;
+        out[2 * ns + n] = hz;
+        return;
+    }
+    T kx = 0, ky = 0, kz = 0;
+    if (magnetic) {
+        const T ax = my * hz - mz * hy, ay = mz * hx - mx * hz, az = mx * hy - my * hx;
+        const T bx = my * az - mz * ay, by = mz * ax - mx * az, bz = mx * ay - my * ax;
+        kx = -p.gam_t * (ax + p.alpha_t * bx);
+        ky = -p.gam_t * (ay + p.alpha_t * by);
+        kz = -p.gam_t * (az + p.alpha_t * bz);
+    }
+    out[n] = kx;
+    out[ns + n] = ky;
+    out[2 * ns + n] = kz;
+    if (y_next) {
+        T px = 0, py = 0, pz = 0;
+        for (int j = 0; j + 1 < sa.s && j < 7; ++j) {
+            const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
+            if (aj == T(0)) continue;
+            const T *kj = (const T *)sa.k[j];
+            px += aj * kj[n];
+            py += aj * kj[ns + n];
+            pz += aj * kj[2 * ns + n];
+        }
+        const T as = sizeof(T) == 4 ? (T)sa.af_s : (T)sa.a_s;
+        px += as * kx;
+        py += as * ky;
+        pz += as * kz;
+        const double dt = sa.ctl ? sa.ctl->dt : 0.0;
+        if (sizeof(T) == 4 && sa.mf) {
+            const float dtf = (float)dt;
+            y_next[n] = (T)(sa.mf[n] + dtf * (float)px);
+            y_next[ns + n] = (T)(sa.mf[ns + n] + dtf * (float)py);
+            y_next[2 * ns + n] = (T)(sa.mf[2 * ns + n] + dtf * (float)pz);
+        } else {
+            y_next[n] = (T)(sa.m[n] + dt * (double)px);
+            y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)py);
+            y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)pz);
+        }
+    }
+}
+
 template <typename T>
 static dim3 node_grid(const Geom &g, int *zc)
 {
@@ -426,6 +570,11 @@ static dim3 node_grid(const Geom &g, int *zc)
 template <typename T>
 void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaStream_t st)
 {
+    if (p.g.basis == 2) {
+        k_node2d<T, false><<<dim3(div_up(p.g.nn1, 32), div_up(p.g.nn2, 8)), 256, 0, st>>>(p, y, h_out, nullptr,
+                                                                                          StageArgs{}, t);
+        return;
+    }
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
     k_node<T, false><<<grid, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
@@ -434,6 +583,11 @@ void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaSt
 template <typename T>
 void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, const StageArgs &sa, cudaStream_t st)
 {
+    if (p.g.basis == 2) {
+        k_node2d<T, true><<<dim3(div_up(p.g.nn1, 32), div_up(p.g.nn2, 8)), 256, 0, st>>>(p, y, k_out, y_next, sa,
+                                                                                         0.0);
+        return;
+    }
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
     k_node<T, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
@@ -451,10 +605,20 @@ __global__ void k_mass(Geom g, const double *__restrict__ Ms, double Ms0, double
     const int n2 = (int)(r % g.nn2);
     const int n3 = (int)(r / g.nn2);
     double s = 0.0;
-    for (int i = 0; i < 8; ++i) {
-        int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
-        if (c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3)
-            s += Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0;
+    if (g.basis == 2) {
+        // the 2D basis function of the node column is constant along z: the 4 in-plane cells of every
+        // layer hold it, each with integral V/4 (twice the 3D corner share)
+        for (int i = 0; i < 4; ++i) {
+            const int c1 = n1 - ((i >> 1) & 1), c2 = n2 - (i & 1);
+            if (c1 < 0 || c1 >= g.N1 || c2 < 0 || c2 >= g.N2) continue;
+            for (int c3 = 0; c3 < g.N3; ++c3) s += 2.0 * (Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0);
+        }
+    } else {
+        for (int i = 0; i < 8; ++i) {
+            int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+            if (c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3)
+                s += Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0;
+        }
     }
     double mass = mu0V8 * s;
     inv_mass[n] = mass > 0.0 ? (T)(1.0 / mass) : T(0);

@@ -21,6 +21,9 @@ struct LocalParams {
     // offset is this times the number of mesh cells that hold both nodes, a product of per-axis counts
     T wexd[8], wand[8];
     T mu0V8;           // mu0 * V / 8
+    // 2D basis (section "Low-Dimensional Geometries"): the in-plane pattern integrals per cell layer
+    // (pattern d = 2 |o1| + |o2|), through the layer's thickness, and mu0 V / 4
+    T Wex2[4], Wm2[4], mu0V4;
     const T *A;        // cell maps (n_cells) or NULL for the uniform value
     const T *Ku;
     const T *Ms;

@@ -110,7 +110,7 @@ void *mapped_host(const void *p);  // device address of mapped page-locked host 
 // nm_create_mesh; with tensor_src a mesh of the same shape, cell size and precision, the twiddles and
 // the tensor spectrum are copied from it on the device instead of being rebuilt
 int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, void *cuda_stream,
-                nm_mesh tensor_src, nm_mesh *out);
+                nm_mesh tensor_src, nm_mesh *out, int basis = 3);
 long mesh_footprint(int n1, int n2, int n3, int precision);
 int pull_ctl(nm_mesh M);
 int push_ctl(nm_mesh M);
@@ -174,6 +174,14 @@ inline LocalParams<T> local_params(nm_mesh M, unsigned terms)
         p.Wm[d] = (T)mm;
     }
     p.mu0V8 = (T)(kMu0 * V / 8.0);
+    p.mu0V4 = (T)(kMu0 * V / 4.0);
+    for (int d = 0; d < 4; ++d) {
+        const int d1 = (d >> 1) & 1, d2 = d & 1;
+        const double M1x = dx[0] * (d1 ? 1.0 / 6.0 : 1.0 / 3.0), M1y = dx[1] * (d2 ? 1.0 / 6.0 : 1.0 / 3.0);
+        const double K1x = (d1 ? -1.0 : 1.0) / dx[0], K1y = (d2 ? -1.0 : 1.0) / dx[1];
+        p.Wex2[d] = (T)(2.0 * (K1x * M1y + M1x * K1y) * dx[2]);
+        p.Wm2[d] = (T)(M1x * M1y * dx[2]);
+    }
     p.A = (const T *)M->A_d;
     p.Ku = (const T *)M->Ku_d;
     p.Ms = (const T *)M->Ms_d;

@@ -572,7 +572,8 @@ __global__ void k_convert(long n, const Tin *__restrict__ a, Tout *__restrict__ 
     if (i < n) b[i] = (Tout)a[i];
 }
 
-// volume weights of the nodal mean: sum over adjacent magnetic cells of V/8
+// volume weights of the nodal mean: sum over adjacent magnetic cells of V/8 (V/4 per in-plane cell and
+// layer with the 2D basis)
 template <typename T>
 __global__ void k_node_volume(Geom g, const double *__restrict__ Ms, double Ms0, double V8, T *vol)
 {
@@ -583,11 +584,20 @@ __global__ void k_node_volume(Geom g, const double *__restrict__ Ms, double Ms0,
     const int n2 = (int)(r % g.nn2);
     const int n3 = (int)(r / g.nn2);
     double s = 0.0;
-    for (int i = 0; i < 8; ++i) {
-        int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
-        if (c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3) {
-            double ms = Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0;
-            if (ms > 0.0) s += V8;
+    if (g.basis == 2) {  // 2D basis: the 4 in-plane cells of every layer, V/4 each
+        for (int i = 0; i < 4; ++i) {
+            const int c1 = n1 - ((i >> 1) & 1), c2 = n2 - (i & 1);
+            if (c1 < 0 || c1 >= g.N1 || c2 < 0 || c2 >= g.N2) continue;
+            for (int c3 = 0; c3 < g.N3; ++c3)
+                if ((Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0) > 0.0) s += 2.0 * V8;
+        }
+    } else {
+        for (int i = 0; i < 8; ++i) {
+            int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+            if (c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3) {
+                double ms = Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0;
+                if (ms > 0.0) s += V8;
+            }
         }
     }
     vol[n] = (T)s;
