@@ -30,6 +30,7 @@ _lib = None
 MU0 = 4e-7 * np.pi
 EXCH, ANIS, ZEE, DEMAG = 1, 2, 4, 8
 ALL = EXCH | ANIS | ZEE | DEMAG
+DMI = 16  # interfacial DMI (a reading: the paper names antisymmetric exchange without its energy)
 
 
 def build(force: bool = False) -> str:
@@ -55,6 +56,7 @@ def _load():
         lib.or_free.argtypes = [vp]
         lib.or_set_material.argtypes = [vp, P, P, P, P, d, d]
         lib.or_set_zeeman.argtypes = [vp, P, d, d, P, d, d]
+        lib.or_set_dmi.argtypes = [vp, P]
         lib.or_mass.argtypes = [vp, P]
         lib.or_newell.argtypes = [d, d, d, d, d, d, P]
         lib.or_compute_tensor.argtypes = [vp]
@@ -154,6 +156,11 @@ class Mesh:
         hc = None if h_cell is None else _f64(h_cell, self.cells + (3,))
         self._lib.or_set_zeeman(self._h, _p(hu), float(freq), float(phase),
                                 None if hc is None else _p(hc), float(cell_freq), float(cell_phase))
+
+    def set_dmi(self, D):
+        """Interfacial DMI constant D (J/m^2), scalar or per cell: E = int D [m_z div m - (m.grad) m_z]."""
+        Dc = _f64(np.broadcast_to(np.asarray(D, dtype=np.float64), self.cells))
+        self._lib.or_set_dmi(self._h, _p(Dc))
 
     # -- fields -------------------------------------------------------------------------------
     def _m(self, m):

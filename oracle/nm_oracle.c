@@ -39,6 +39,7 @@
 #define TERM_ANIS 2u
 #define TERM_ZEE 4u
 #define TERM_DEMAG 8u
+#define TERM_DMI 16u
 
 typedef _Float128 q128;
 
@@ -54,6 +55,8 @@ typedef struct {
     double Kex[8][8];                         /* int_cell 2 grad(phi_i).grad(phi_i') */
     double Mm[8][8];                          /* int_cell phi_i phi_i' */
     double Phi[8];                            /* int_cell phi_i */
+    double *D;                                /* interfacial DMI constant per cell (J/m^2) */
+    double Gd[2][8][8];                       /* int_cell phi_i d_k phi_i', k = x, y */
 } OrMesh;
 
 /* ------------------------------------------------------------------------------------------------
@@ -154,14 +157,37 @@ void *or_create(int n1, int n2, int n3, double dx1, double dx2, double dx3)
     o->alpha = 0.0;
     o->gamma = 0.0;
     or_element_matrices(dx1, dx2, dx3, &o->Kex[0][0], &o->Mm[0][0], o->Phi);
+    o->D = (double *)calloc(nc, sizeof(double));
+    {
+        const double V = dx1 * dx2 * dx3;
+        for (int q = 0; q < 8; ++q) {
+            double xi[3], w;
+            gauss_point(q, xi, &w);
+            for (int li = 0; li < 8; ++li)
+                for (int lj = 0; lj < 8; ++lj) {
+                    double gj[3];
+                    grad_phi(lj, xi, o->dx, gj);
+                    const double pi = or_phi(li, xi[0], xi[1], xi[2]);
+                    for (int k = 0; k < 2; ++k) o->Gd[k][li][lj] += w * V * pi * gj[k];
+                }
+        }
+    }
     return o;
+}
+
+/* Interfacial Dzyaloshinskii-Moriya constant per cell (J/m^2); the energy is the reading
+ *   E = int D [m_z div m - (m . grad) m_z]  (interface normal along z). */
+void or_set_dmi(void *h, const double *D)
+{
+    OrMesh *o = (OrMesh *)h;
+    memcpy(o->D, D, n_cells(o) * sizeof(double));
 }
 
 void or_free(void *h)
 {
     OrMesh *o = (OrMesh *)h;
     if (!o) return;
-    free(o->Ms); free(o->A); free(o->Ku); free(o->hcell); free(o->Nt);
+    free(o->Ms); free(o->A); free(o->Ku); free(o->hcell); free(o->Nt); free(o->D);
     free(o);
 }
 
@@ -418,6 +444,16 @@ void or_variation(void *h, const double *m, unsigned terms, double t, double *dE
                         }
                     if (terms & TERM_DEMAG)
                         for (int j = 0; j < 3; ++j) d[j] += -MU0 * o->Ms[c] * Hc[3 * c + j] * o->Phi[li];
+                    if ((terms & TERM_DMI) && o->D[c] != 0.0)
+                        /* E_c = D sum_{i,i'} [m_iz G_x(i,i') m_i'x + m_iz G_y(i,i') m_i'y
+                         *                     - m_ix G_x(i,i') m_i'z - m_iy G_y(i,i') m_i'z] */
+                        for (int lj = 0; lj < 8; ++lj) {
+                            const double ax = o->Gd[0][li][lj] - o->Gd[0][lj][li];
+                            const double ay = o->Gd[1][li][lj] - o->Gd[1][lj][li];
+                            d[0] += -o->D[c] * ax * mc[lj][2];
+                            d[1] += -o->D[c] * ay * mc[lj][2];
+                            d[2] += o->D[c] * (ax * mc[lj][0] + ay * mc[lj][1]);
+                        }
                 }
             }
     free(Hc);
@@ -492,6 +528,8 @@ double or_energy(void *h, const double *m, unsigned terms, double t)
                         }
                     if (terms & TERM_DEMAG)
                         for (int j = 0; j < 3; ++j) E += -0.5 * MU0 * o->Ms[c] * Hc[3 * c + j] * mv[j] * dV;
+                    if (terms & TERM_DMI)  /* gm[j][k] = d_k m_j */
+                        E += o->D[c] * (mv[2] * (gm[0][0] + gm[1][1]) - mv[0] * gm[2][0] - mv[1] * gm[2][1]) * dV;
                 }
             }
     free(Hc);
