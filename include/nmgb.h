@@ -59,6 +59,11 @@ extern "C" {
 #define NM_ZEE 4u
 #define NM_DEMAG 8u
 #define NM_ALL 15u
+/* interfacial DMI (set with nm_set_dmi; not in NM_ALL).  A reading: the paper lists antisymmetric
+ * exchange among the energies its scheme handles (section "Nodal Finite-Difference Scheme") without
+ * giving one; this library takes E = int D [m_z div m - (m . grad) m_z] (interface normal along z). */
+#define NM_DMI 16u
+#define NM_TERMS_MASK 31u
 
 /* integrators */
 #define NM_RK4 1   /* classical Runge-Kutta, fixed step */
@@ -122,14 +127,22 @@ int nm_get_state(nm_mesh mesh, double *m_out, int where, double *t, double *dt);
  * (default 50). */
 int nm_set_integrator(nm_mesh mesh, int renormalise, double dt_min, int max_rejections);
 
-/* Effective field h = H_eff(m) at time t for the terms in the mask (NM_EXCH|NM_ANIS|NM_ZEE|NM_DEMAG):
+/* Effective field h = H_eff(m) at time t for the terms in the mask (NM_EXCH|NM_ANIS|NM_ZEE|NM_DEMAG|NM_DMI):
  * m and h_out are DEVICE pointers to real nodal vector fields; m == NULL uses the resident state.
  * Nodes that touch no magnetic cell get h = 0.  Asynchronous.  Errors: NM_ERR_ARG, NM_ERR_STATE
  * (material not set), NM_ERR_CUDA. */
 int nm_h_eff(nm_mesh mesh, const void *m, void *h_out, unsigned terms, double t);
 
-/* Select the field terms used by the integrators (default NM_ALL). */
+/* Select the field terms used by the integrators (default NM_ALL; add NM_DMI for the DMI term). */
 int nm_set_terms(nm_mesh mesh, unsigned terms);
+
+/* Interfacial DMI constant (J/m^2): D is a HOST FP64 cell scalar field (N1, N2, N3), or NULL for the
+ * uniform value D0.  The term enters the field and the integrators when NM_DMI is in the term mask:
+ * its variation is assembled cell by cell from the element integrals int phi_i d_k phi_i' (k = x, y) of
+ * the trilinear basis, like the exchange (Eqs. weak_form_impl_f, weak_form_impl), over magnetic cells,
+ * and divided by the lumped mass.  Needs the 3D basis.  Errors: NM_ERR_ARG (non-finite values, a
+ * basis-2 mesh), NM_ERR_OOM, NM_ERR_CUDA. */
+int nm_set_dmi(nm_mesh mesh, const double *D, double D0);
 
 /* One integrator step on the resident state.  NM_RK4 uses *dt as the fixed step; NM_DP54 attempts
  * *dt and on return *dt holds the proposed next step, *accepted tells whether the attempt was taken

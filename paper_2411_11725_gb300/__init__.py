@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "Mesh", "NMError", "load", "lib_path",
-    "F32", "F64", "EXCH", "ANIS", "ZEE", "DEMAG", "ALL", "RK4", "DP54",
+    "F32", "F64", "EXCH", "ANIS", "ZEE", "DEMAG", "ALL", "DMI", "RK4", "DP54",
 ]
 
 OK = 0
@@ -28,6 +28,7 @@ ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STEP_UNDERFLOW, ERR_NONFINITE, ERR_TIMEOUT, ERR_
 F32, F64 = 0, 1
 EXCH, ANIS, ZEE, DEMAG = 1, 2, 4, 8
 ALL = EXCH | ANIS | ZEE | DEMAG
+DMI = 16  # interfacial DMI (nm_set_dmi); not part of ALL
 RK4, DP54 = 1, 2
 FIELD_HEXT_UNIFORM, FIELD_HEXT_CELL = 1, 2
 MEM_HOST, MEM_DEVICE = 0, 1
@@ -85,6 +86,7 @@ SIGNATURES = [
     ("nm_set_integrator", _i, [_vp, _i, _d, _i]),
     ("nm_h_eff", _i, [_vp, _vp, _vp, _u, _d]),
     ("nm_set_terms", _i, [_vp, _u]),
+    ("nm_set_dmi", _i, [_vp, _Pd, _d]),
     ("nm_llg_step", _i, [_vp, _i, _Pd, _Pd, _d, _d, _Pi]),
     ("nm_run_steps", _i, [_vp, _i, _l, _d, _d]),
     ("nm_get_counters", _i, [_vp, _Pl, _Pl, _Pd]),
@@ -214,6 +216,14 @@ class Mesh:
         ax = _host_f64(axis, (3,))
         _check(self.lib.nm_set_material(self._h, _pd(Ms_a), Ms0, _pd(A_a), A0, _pd(Ku_a), Ku0, _pd(ax),
                                         float(alpha), float(gamma)))
+
+    def set_dmi(self, D):
+        """Interfacial DMI constant (J/m^2): scalar or cell map (N1, N2, N3); enable with DMI in the terms."""
+        if np.ndim(D) == 0:
+            _check(self.lib.nm_set_dmi(self._h, None, float(D)))
+        else:
+            Dc = _host_f64(D, self.n)
+            _check(self.lib.nm_set_dmi(self._h, _pd(Dc), 0.0))
 
     def set_zeeman(self, h_uniform=(0.0, 0.0, 0.0), freq=0.0, phase=0.0, h_cell=None, cell_freq=0.0,
                    cell_phase=0.0):

@@ -106,7 +106,7 @@ extern "C" int nm_h_eff_vjp(nm_mesh M, const void *m, const void *v, unsigned te
 {
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     if (!m || !v || !grad_m) return fail(NM_ERR_ARG, "m, v and grad_m are required");
-    if (terms & ~NM_ALL) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
+    if (terms & ~NM_TERMS_MASK) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
     if (!isfinite(t)) return fail(NM_ERR_ARG, "t must be finite");
     if (!M->material_set) return fail(NM_ERR_STATE, "material not set");
     if (M->g.basis != 3) return fail(NM_ERR_ARG, "the transpose product needs the 3D nodal basis");

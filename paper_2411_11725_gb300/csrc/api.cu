@@ -142,7 +142,8 @@ static void release(nm_mesh M)
     cudaStreamSynchronize(M->st);
     free_graphs(M);
     void *ptrs[] = {M->m, M->mf, M->y[0], M->y[1], M->hin, M->hout, M->inv_mass, M->vol, M->MsH, M->S, M->Nk, M->tw,
-                    M->tw64, M->A_d, M->Ku_d, M->Ms_d, M->Ms64_d, M->Msh_d, M->hcell64_d, M->ctl, M->partials,
+                    M->tw64, M->A_d, M->Ku_d, M->Ms_d, M->Ms64_d, M->Msh_d, M->hcell64_d, M->D_d, M->hdmi, M->ctl,
+                    M->partials,
                     M->mean_d, M->n_active_d, M->vj_w, M->vj_h, M->vj_q, M->vj_g, M->vj_H, M->vj_HW, M->vj_M,
                     M->vj_gMs};
     for (void *p : ptrs)
@@ -396,6 +397,38 @@ static int set_material_t(nm_mesh M, const double *Ms, const double *A, const do
 
 static int rebuild_cell_field(nm_mesh M);
 
+template <typename T>
+static int set_dmi_t(nm_mesh M, const double *D)
+{
+    int rc;
+    if (D) {
+        if ((rc = upload_cells<T>(M, D, 1, &M->D_d, false, nullptr))) return rc;
+    } else if (M->D_d) {
+        cudaFree(M->D_d);
+        M->D_d = nullptr;
+    }
+    if (!M->hdmi && (rc = dev_alloc(M, &M->hdmi, 3 * M->g.ns * sizeof(T)))) return rc;
+    CUDA_TRY(cudaMemsetAsync(M->hdmi, 0, 3 * M->g.ns * sizeof(T), M->st));
+    return NM_OK;
+}
+
+extern "C" int nm_set_dmi(nm_mesh M, const double *D, double D0)
+{
+    g_last_error.clear();
+    if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
+    if (M->g.basis != 3) return fail(NM_ERR_ARG, "the DMI term needs the 3D nodal basis");
+    double mn;
+    if (D && !all_finite(D, M->g.n_cells, &mn)) return fail(NM_ERR_ARG, "D map must be finite");
+    if (!D && !isfinite(D0)) return fail(NM_ERR_ARG, "D0 must be finite");
+    free_graphs(M);
+    int rc = M->prec == NM_F64 ? set_dmi_t<double>(M, D) : set_dmi_t<float>(M, D);
+    if (rc) return rc;
+    M->D0 = D ? 0.0 : D0;
+    M->has_dmi = true;
+    M->k1_valid = false;
+    return NM_OK;
+}
+
 extern "C" int nm_set_material(nm_mesh M, const double *Ms, double Ms0, const double *A, double A0,
                                const double *Ku, double Ku0, const double axis[3], double alpha, double gamma)
 {
@@ -492,7 +525,7 @@ extern "C" int nm_set_field(nm_mesh M, int kind, const double *data, const doubl
 extern "C" int nm_set_terms(nm_mesh M, unsigned terms)
 {
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
-    if (terms & ~NM_ALL) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
+    if (terms & ~NM_TERMS_MASK) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
     M->terms = terms;
     M->k1_valid = false;
     free_graphs(M);
@@ -629,7 +662,7 @@ extern "C" int nm_h_eff(nm_mesh M, const void *m, void *h_out, unsigned terms, d
     g_last_error.clear();
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     if (!h_out) return fail(NM_ERR_ARG, "h_out is NULL");
-    if (terms & ~NM_ALL) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
+    if (terms & ~NM_TERMS_MASK) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
     if (!isfinite(t)) return fail(NM_ERR_ARG, "t must be finite");
     if (!M->material_set) return fail(NM_ERR_STATE, "material not set");
     if (!m && !M->state_set) return fail(NM_ERR_STATE, "m is NULL and no resident state");

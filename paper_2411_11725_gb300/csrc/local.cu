@@ -292,7 +292,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 
 // STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
 // input.  Block (bx, by, bz) covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [bz*zc, bz*zc+zc).
-template <typename T, bool STAGE>
+template <typename T, bool STAGE, bool DMI = false>
 __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 4 : 3) k_node(LocalParams<T> p, const T *__restrict__ y,
                                                         T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
                                                         double t_heff, int zc)
@@ -341,6 +341,12 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 4 : 3) k_node(Lo
         const int n = (z * g.nn2 + n2) * g.nn1 + n1;
         T im = T(0), px = 0, py = 0, pz = 0;
         float mfx = 0.f, mfy = 0.f, mfz = 0.f;
+        T dmx = 0, dmy = 0, dmz = 0;  // raw DMI field of this node (DMI instances)
+        if (DMI && active) {
+            dmx = p.hdmi[n];
+            dmy = p.hdmi[ns + n];
+            dmz = p.hdmi[2 * ns + n];
+        }
         if (active) {
             im = p.inv_mass[n];
             if (STAGE && y_next) {
@@ -365,9 +371,15 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 4 : 3) k_node(Lo
         __syncthreads();
         const bool interior = tile_inner && z >= 1 && z <= g.N3 - 1;
         if (active) {
-            const NodeField<T> f = interior    ? node_field<T, 1>(p, sm, n1, n2, z, im, tx, ty)
-                                   : p.uniform ? node_field<T, 2>(p, sm, n1, n2, z, im, tx, ty)
-                                               : node_field<T, 0>(p, sm, n1, n2, z, im, tx, ty);
+            NodeField<T> f = interior    ? node_field<T, 1>(p, sm, n1, n2, z, im, tx, ty)
+                             : p.uniform ? node_field<T, 2>(p, sm, n1, n2, z, im, tx, ty)
+                                         : node_field<T, 0>(p, sm, n1, n2, z, im, tx, ty);
+            if (DMI) {
+                const T sc = p.raw ? T(1) : im;
+                f.hx += sc * dmx;
+                f.hy += sc * dmy;
+                f.hz += sc * dmz;
+            }
             if (!STAGE) {
                 out[n] = f.hx;
                 out[ns + n] = f.hy;
@@ -556,6 +568,65 @@ __global__ void __launch_bounds__(256) k_node2d(LocalParams<T> p, const T *__res
     }
 }
 
+// Interfacial DMI, E = int D [m_z div m - (m . grad) m_z] (a reading of the paper's "antisymmetric
+// exchange"), assembled like the exchange: with G_k(i,i') = int_cell phi_i d_k phi_i' and its
+// antisymmetric part A_k, node n couples to n + o through every magnetic cell holding both nodes,
+//   A_x(n, n+o) = o1 (mass integrals along y, z of the pattern),  A_y(n, n+o) = o2 (along x, z),
+//   dE_x = -sum_o S_o A_x m_{n+o,z},  dE_y = -sum_o S_o A_y m_{n+o,z},
+//   dE_z = sum_o S_o (A_x m_{n+o,x} + A_y m_{n+o,y}),        S_o = sum_{cells} D_c.
+// Writes the raw field -dE per node (the node kernel scales it by 1/mass).  One thread per node,
+// neighbours through L1.
+template <typename T>
+__global__ void __launch_bounds__(256) k_dmi(LocalParams<T> p, const T *__restrict__ y, T *__restrict__ out)
+{
+    const Geom &g = p.g;
+    const long n = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (n >= g.n_nodes) return;
+    const int n1 = (int)(n % g.nn1);
+    const long r = n / g.nn1;
+    const int n2 = (int)(r % g.nn2), n3 = (int)(r / g.nn2);
+    const long ns = g.ns;
+    T Dc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c1 = n1 - ((i >> 2) & 1), c2 = n2 - ((i >> 1) & 1), c3 = n3 - (i & 1);
+        const bool valid = c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2 && c3 >= 0 && c3 < g.N3;
+        const int c = valid ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
+        const T Ms = valid ? (p.Ms ? p.Ms[c] : p.Ms0) : T(0);
+        Dc[i] = (valid && Ms > T(0)) ? (p.Dm ? p.Dm[c] : p.D0) : T(0);
+    }
+    T ex = 0, ey = 0, ez = 0;
+#pragma unroll
+    for (int o3 = -1; o3 <= 1; ++o3)
+#pragma unroll
+        for (int o2 = -1; o2 <= 1; ++o2)
+#pragma unroll
+            for (int o1 = -1; o1 <= 1; ++o1) {
+                if (o1 == 0 && o2 == 0) continue;  // no in-plane derivative couples them
+                T S = 0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
+                    const bool both = (o1 == -1 ? i1 == 1 : (o1 == 1 ? i1 == 0 : true)) &&
+                                      (o2 == -1 ? i2 == 1 : (o2 == 1 ? i2 == 0 : true)) &&
+                                      (o3 == -1 ? i3 == 1 : (o3 == 1 ? i3 == 0 : true));
+                    if (both) S += Dc[i];
+                }
+                const int q1 = n1 + o1, q2 = n2 + o2, q3 = n3 + o3;
+                if (q1 < 0 || q1 >= g.nn1 || q2 < 0 || q2 >= g.nn2 || q3 < 0 || q3 >= g.nn3) continue;
+                const long q = ((long)q3 * g.nn2 + q2) * g.nn1 + q1;
+                const T ax = o1 == 0 ? T(0) : T(o1) * p.dmx[2 * (o2 != 0) + (o3 != 0)] * S;
+                const T ay = o2 == 0 ? T(0) : T(o2) * p.dmy[2 * (o1 != 0) + (o3 != 0)] * S;
+                const T qx = y[q], qy = y[ns + q], qz = y[2 * ns + q];
+                ex += -ax * qz;
+                ey += -ay * qz;
+                ez += ax * qx + ay * qy;
+            }
+    out[n] = -ex;
+    out[ns + n] = -ey;
+    out[2 * ns + n] = -ez;
+}
+
 template <typename T>
 static dim3 node_grid(const Geom &g, int *zc)
 {
@@ -577,6 +648,11 @@ void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaSt
     }
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
+    if (p.hdmi) {
+        k_dmi<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, p.hdmi);
+        k_node<T, false, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
+        return;
+    }
     k_node<T, false><<<grid, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
 }
 
@@ -590,6 +666,11 @@ void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, 
     }
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
+    if (p.hdmi) {
+        k_dmi<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, p.hdmi);
+        k_node<T, true, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
+        return;
+    }
     k_node<T, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
 }
 

@@ -24,6 +24,11 @@ struct LocalParams {
     // 2D basis (section "Low-Dimensional Geometries"): the in-plane pattern integrals per cell layer
     // (pattern d = 2 |o1| + |o2|), through the layer's thickness, and mu0 V / 4
     T Wex2[4], Wm2[4], mu0V4;
+    // interfacial DMI: raw field buffer (NULL: term off), cell map or uniform value, and the pattern
+    // weights of the antisymmetric element integrals (dmx by (|o2|,|o3|), dmy by (|o1|,|o3|))
+    T *hdmi;
+    const T *Dm;
+    T D0, dmx[4], dmy[4];
     const T *A;        // cell maps (n_cells) or NULL for the uniform value
     const T *Ku;
     const T *Ms;

@@ -72,6 +72,10 @@ struct nm_mesh_s {
     void *A_d = nullptr, *Ku_d = nullptr, *Ms_d = nullptr;
     double *Ms64_d = nullptr;
     void *Msh_d = nullptr;
+    void *D_d = nullptr;       // interfacial DMI per cell (working precision) or NULL: uniform D0
+    void *hdmi = nullptr;      // raw DMI field -dE_DMI at the current stage input (3 x ns)
+    double D0 = 0.0;
+    bool has_dmi = false;
     double *hcell64_d = nullptr;
     StepCtl *ctl = nullptr;
     StepCtl *hctl = nullptr;  // pinned host mirror
@@ -192,6 +196,15 @@ inline LocalParams<T> local_params(nm_mesh M, unsigned terms)
     p.inv_mass = (const T *)M->inv_mass;
     p.MsH = (terms & NM_DEMAG) ? (const T *)M->MsH : nullptr;
     p.Msh = M->has_hcell ? (const T *)M->Msh_d : nullptr;
+    p.hdmi = (M->has_dmi && (terms & NM_DMI) && M->g.basis == 3) ? (T *)M->hdmi : nullptr;
+    p.Dm = (const T *)M->D_d;
+    p.D0 = (T)M->D0;
+    for (int d = 0; d < 4; ++d) {
+        // DMI weights: int phi_i d_x phi_i' = o1 * (y, z mass integrals of the pattern), o1 = i1' - i1
+        const int a = (d >> 1) & 1, b = d & 1;
+        p.dmx[d] = (T)(dx[1] * (a ? 1.0 / 6.0 : 1.0 / 3.0) * dx[2] * (b ? 1.0 / 6.0 : 1.0 / 3.0));  // (|o2|, |o3|)
+        p.dmy[d] = (T)(dx[0] * (a ? 1.0 / 6.0 : 1.0 / 3.0) * dx[2] * (b ? 1.0 / 6.0 : 1.0 / 3.0));  // (|o1|, |o3|)
+    }
     p.hu0 = M->hu[0]; p.hu1 = M->hu[1]; p.hu2 = M->hu[2];
     p.hu_freq = M->hu_freq; p.hu_phase = M->hu_phase;
     p.hc_freq = M->hc_freq; p.hc_phase = M->hc_phase;

@@ -376,7 +376,7 @@ int check_request(const nm_request *q)
     if (!(q->axis[0] * q->axis[0] + q->axis[1] * q->axis[1] + q->axis[2] * q->axis[2] > 0))
         return fail(NM_ERR_ARG, "axis must be non-zero");
     if (!isfinite(q->alpha) || q->alpha < 0 || !isfinite(q->gamma)) return fail(NM_ERR_ARG, "alpha/gamma invalid");
-    if (q->terms & ~NM_ALL) return fail(NM_ERR_ARG, "unknown term bits 0x%x", q->terms);
+    if (q->terms & ~NM_TERMS_MASK) return fail(NM_ERR_ARG, "unknown term bits 0x%x", q->terms);
     if (q->method != NM_RK4 && q->method != NM_DP54) return fail(NM_ERR_ARG, "unknown method %d", q->method);
     if (!(q->t_end > 0) || !isfinite(q->t_end)) return fail(NM_ERR_ARG, "t_end must be positive and finite");
     if (!(q->dt0 > 0) || !isfinite(q->dt0)) return fail(NM_ERR_ARG, "dt0 must be positive and finite");
