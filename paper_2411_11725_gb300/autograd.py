@@ -10,6 +10,10 @@ sizes frozen); ``backward`` hands the stored gradients to autograd.  With ``h`` 
 set on the mesh (frequency and phase from the spec) and dL/dh is returned too, so that field
 parameters such as the angles of the paper's inverse problem (section "Inverse Problems") can be
 optimised through autograd.
+
+With ``spec.adjoint = "continuous"`` the gradients come from the continuous adjoint-state method
+instead (Eq. adjoint_system): a final-time loss, round((t_end - t0) / dt0) classical Runge-Kutta steps
+forward, and the adjoint system integrated backwards (nm_adjoint_continuous).
 """
 from __future__ import annotations
 
@@ -42,6 +46,7 @@ class LossSpec:
     t0: float = 0.0
     h_freq: float = 0.0      # time dependence of the uniform field when h is passed to llg_loss
     h_phase: float = 0.0
+    adjoint: str = "discrete"  # or "continuous" (final-time loss, RK4 steps of dt0)
     stats: dict = field(default_factory=dict)
 
 
@@ -54,9 +59,17 @@ class _LLGLoss(torch.autograd.Function):
         if h is not None:
             mesh.set_uniform_field(h.detach().to("cpu", torch.float64).numpy(), spec.h_freq, spec.h_phase)
         mesh.set_state(m0_h, spec.t0, spec.dt0)
-        loss, gMs, gm0, n, gh = mesh.adjoint_run(spec.t_end, weight, spec.target, spec.method, spec.rtol,
-                                                 spec.atol, spec.dt0, spec.sample_dt, spec.include_initial,
-                                                 spec.checkpoint_every, field_grad=True)
+        if spec.adjoint == "continuous":
+            if spec.sample_dt > 0 or spec.include_initial:
+                raise ValueError("the continuous adjoint takes a final-time loss (sample_dt = 0, no initial term)")
+            n = max(1, int(round((spec.t_end - spec.t0) / spec.dt0)))
+            loss, gm0, gMs, gh, _ = mesh.adjoint_continuous(spec.t_end, n, weight, spec.target)
+        elif spec.adjoint == "discrete":
+            loss, gMs, gm0, n, gh = mesh.adjoint_run(spec.t_end, weight, spec.target, spec.method, spec.rtol,
+                                                     spec.atol, spec.dt0, spec.sample_dt, spec.include_initial,
+                                                     spec.checkpoint_every, field_grad=True)
+        else:
+            raise ValueError(f"unknown adjoint {spec.adjoint!r}")
         spec.stats["accepted_steps"] = n
         gh_t = torch.from_numpy(gh).to(h.device, h.dtype) if h is not None else torch.zeros(3)
         ctx.save_for_backward(torch.from_numpy(gMs).to(Ms.device, Ms.dtype),

@@ -67,7 +67,7 @@ struct YTile {
     static_assert(G * P2 <= EPT * THREADS && THREADS <= MAXT, "y tile exceeds the block");
 };
 
-// forward x pass: radix-16 stages for FP32 lines of 2^10 complex values (the inverse keeps 8: measured)
+// x passes: radix-16 stages for FP32 lines of 2^10 complex values
 template <typename T, int LG>
 constexpr int kXEpt = (sizeof(T) == 4 && LG >= 10) ? 16 : 8;
 // the single-layer pass keeps up to 1024 threads (FP32) so that long y lines still fit one block
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 4 : 2)
         out[xi.in + x] = v0;
         if (x + 1 < N1) out[xi.in + x + 1] = v1;
     };
-    f3::fft<T, LG, +1, false, true, false>(buf, nl, FastDiv(1u), b.tw, g.twlg, Q, (N1 + 1) >> 1, f3::NoFn<T>(), dst);
+    f3::fft<T, LG, +1, false, true, false, kXEpt<T, LG>>(buf, nl, FastDiv(1u), b.tw, g.twlg, Q, (N1 + 1) >> 1, f3::NoFn<T>(), dst);
 }
 
 template <typename T, bool CELL_OUT>
@@ -712,7 +712,7 @@ DemagPlan demag_plan(const Geom &g)
         p.x_lpb = lpb < 1 ? 1 : lpb;
         p.x_threads = kXThreads;
         p.x_smem = (size_t)p.x_lpb * f3::padded(g.Q) * cs + (size_t)p.x_lpb * 3 * sizeof(int);
-        int lpbi = (int)(8L * kXThreads / g.Q);  // the inverse transform keeps 8 values per thread
+        int lpbi = (int)((long)xept * kXThreads / g.Q);  // the inverse takes the same stages (measured)
         lpbi = lpbi > 64 ? 64 : lpbi;
         if (lpbi < 1) p.ok = false;
         p.xi_lpb = lpbi < 1 ? 1 : lpbi;
@@ -764,7 +764,7 @@ DemagPlan demag_plan(const Geom &g)
     // every block holds at most (values per thread) x (threads) values of its transforms
     if (g.P1 > 1) {
         const long xept = (sizeof(T) == 4 && g.lgQ >= 10) ? 16 : 8;
-        if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > 8L * p.x_threads) p.ok = false;
+        if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > xept * p.x_threads) p.ok = false;
     }
     if (g.N3 > 1) {
         if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) ||
