@@ -42,7 +42,7 @@ struct DemagPlan {
     bool ok;  // the grid fits the engine's per-block budget in this precision
     int x_lpb, x_threads;      // forward x pass
     size_t x_smem;
-    int xi_lpb;                // inverse x pass (same threads)
+    int xi_lpb, xi_threads;    // inverse x pass
     size_t xi_smem;
     int y_G, y_threads;
     size_t y_smem;

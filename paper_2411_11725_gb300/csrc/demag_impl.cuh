@@ -18,9 +18,12 @@
 
 namespace nm {
 
-// x passes: 128-thread blocks of two 1024-point lines, eight per SM in FP32 (measured against 256 and 512
-// threads: the small blocks hide the gather and barrier latency best)
+// x passes: small blocks hide the gather and barrier latency best (measured against 256 and 512
+// threads): the forward pass takes 128 threads (two 1024-point lines, eight blocks per SM), the inverse
+// pass 64 in FP32 (one line, sixteen blocks per SM; FP64 keeps 128 threads for its 8 values per thread)
 constexpr int kXThreads = 128;
+template <typename T>
+constexpr int kXiThreads = sizeof(T) == 4 ? 64 : 128;
 // y and z passes: 512-thread blocks, two per SM in FP32 (one block's loads and barriers overlap the
 // other's arithmetic); the longest y lines (2^11) take 1024 threads so that a block still spans 4 columns.
 template <typename T, int LG = 0>
@@ -218,7 +221,7 @@ __global__ void k_x_fwd1(Geom g, DemagBufs<T> b, const T *__restrict__ in)
 // Pass 5: inverse x transform (C2R of length P1 via a complex FFT of length Q), keeping x < N1.
 // Output per cell: Ms_c H_c (or H_c when CELL_OUT).
 template <typename T, bool CELL_OUT, int LG>
-__global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 8 : 4)
+__global__ void __launch_bounds__(kXiThreads<T>, sizeof(T) == 4 ? 16 : 4)
     k_x_inv(Geom g, DemagBufs<T> b, T *__restrict__ out, int lpb)
 {
     if (b.ctl && b.ctl->done) return;
@@ -714,14 +717,16 @@ DemagPlan demag_plan(const Geom &g)
         p.x_lpb = lpb < 1 ? 1 : lpb;
         p.x_threads = kXThreads;
         p.x_smem = (size_t)p.x_lpb * f3::padded(g.Q) * cs + (size_t)p.x_lpb * 3 * sizeof(int);
-        int lpbi = (int)((long)xept * kXThreads / g.Q);  // the inverse takes the same stages (measured)
+        int lpbi = (int)((long)xept * kXiThreads<T> / g.Q);  // the inverse takes the same stages (measured)
         lpbi = lpbi > 64 ? 64 : lpbi;
         if (lpbi < 1) p.ok = false;
         p.xi_lpb = lpbi < 1 ? 1 : lpbi;
+        p.xi_threads = kXiThreads<T>;
         p.xi_smem = (size_t)p.xi_lpb * f3::padded(g.Q) * cs + (size_t)p.xi_lpb * 3 * sizeof(int);
     } else {
         p.x_lpb = 1;
         p.xi_lpb = 1;
+        p.xi_threads = 256;
         p.xi_smem = 0;
         p.x_threads = 256;
         p.x_smem = 0;
@@ -766,7 +771,7 @@ DemagPlan demag_plan(const Geom &g)
     // every block holds at most (values per thread) x (threads) values of its transforms
     if (g.P1 > 1) {
         const long xept = (sizeof(T) == 4 && g.lgQ >= 10) ? 16 : 8;
-        if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > xept * p.x_threads) p.ok = false;
+        if ((long)p.x_lpb * g.Q > xept * p.x_threads || (long)p.xi_lpb * g.Q > xept * p.xi_threads) p.ok = false;
     }
     if (g.N3 > 1) {
         if (p.y_threads > kMaxThreads<T> * ((sizeof(T) == 4 && g.lgP2 >= 11) ? 2 : 1) ||
@@ -840,7 +845,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
     } else {
         f3::lg_dispatch<1, 10>(g.lgQ, [&](auto c) {
             constexpr int LG = decltype(c)::value;
-            k_x_inv<T, CELL, LG><<<div_up(nlines, p.xi_lpb), p.x_threads, p.xi_smem, st>>>(g, b, out, p.xi_lpb);
+            k_x_inv<T, CELL, LG><<<div_up(nlines, p.xi_lpb), p.xi_threads, p.xi_smem, st>>>(g, b, out, p.xi_lpb);
         });
     }
     b.mark("demag_x_inv");
