@@ -26,7 +26,7 @@ __device__ __forceinline__ double time_factor(double f, double ph, double t)
 // and cells outside the mesh are filled with zeros (their weights are zero too).
 constexpr int kTX = 32;
 template <typename T>
-constexpr int kTY = 4;  // 128-thread tiles, eight FP32 blocks per SM (measured: 6 % faster than 32 x 8 at four)
+constexpr int kTY = 4;  // 128-thread tiles, six FP32 blocks per SM at 80 registers (measured best of 32 x 2/4/8 tiles and 4-8 blocks)
 constexpr int kNodeSlots = 4, kCellSlots = 3;
 
 // a nodal or cell 3-vector in shared memory: padded to one 16-byte access in FP32, packed in FP64
@@ -293,7 +293,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 // STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
 // input.  Block (bx, by, bz) covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [bz*zc, bz*zc+zc).
 template <typename T, bool STAGE, bool DMI = false>
-__global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 8 : 3) k_node(LocalParams<T> p, const T *__restrict__ y,
+__global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(LocalParams<T> p, const T *__restrict__ y,
                                                         T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
                                                         double t_heff, int zc)
 {
