@@ -342,11 +342,15 @@ def run_ours(args, rank, world, dist):
         m_host = torch.from_numpy(m0.copy()).pin_memory()
         me.set_state(m_host.numpy(), 0.0, me.get_state()[2])
         ke = max(2, min(K, args.e2e_steps))
+        dt_e = me.get_state()[2]
+        # one untimed pass of the loop: the step graph is captured again after the per-launch profile
+        me.set_state_host_ptr(m_host, 0.0, dt_e)
+        me.run_steps(1, nmgb.DP54, 1e-5, 1e-5)
+        me.mean_m()
         torch.cuda.synchronize()
         barrier()
         t_e = time.perf_counter()
         acc_e = 0
-        dt_e = me.get_state()[2]
         mean_hist = []
         for _ in range(ke):
             me.set_state_host_ptr(m_host, 0.0, dt_e)
