@@ -75,6 +75,7 @@ def _load():
         lib.or_phi.argtypes = [i, d, d, d]
         lib.or_phi.restype = d
         lib.or_num_threads.restype = i
+        lib.or_set_num_threads.argtypes = [i]
         _lib = lib
         return lib
 
@@ -92,6 +93,11 @@ def _f64(a, shape=None) -> np.ndarray:
 
 def num_threads() -> int:
     return _load().or_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Thread count for the oracle's parallel loops (its results do not depend on it)."""
+    _load().or_set_num_threads(int(n))
 
 
 def phi(li: int, x1: float, x2: float, x3: float) -> float:

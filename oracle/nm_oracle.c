@@ -698,3 +698,14 @@ int or_num_threads(void)
     return 1;
 #endif
 }
+
+/* Thread count of the parallel loops that follow (for timing: each iteration of those loops writes its
+   own outputs from sums taken in a fixed order, so the results do not depend on it). */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}

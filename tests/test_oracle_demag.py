@@ -151,3 +151,23 @@ def test_thin_film_limit(oracle_mod):
     # 1 - O(t/L): for t/L = 1/120 the deficit is below a few percent
     assert 0.97 < hz < 1.0
     assert abs(h[20, 20, 0, 0]) < 1e-9 * Ms and abs(h[20, 20, 0, 1]) < 1e-9 * Ms
+
+
+def test_results_do_not_depend_on_the_thread_count(oracle_mod):
+    """The direct-sum field and the tensor are bitwise the same on one host thread and on all of them
+    (the CPU baseline is timed both ways)."""
+    rng = np.random.default_rng(12)
+    p = inp.random_problem(rng, (6, 5, 3))
+    me = oracle_mod.Mesh(p.n, p.dx)
+    me.set_material(p.Ms_cells(), p.A_cells(), p.Ku_cells(), p.axis, p.alpha, p.gamma)
+    all_threads = oracle_mod.num_threads()
+    h_all = me.h_eff(p.m0, oracle_mod.DEMAG)
+    try:
+        oracle_mod.set_num_threads(1)
+        assert oracle_mod.num_threads() == 1
+        me1 = oracle_mod.Mesh(p.n, p.dx)
+        me1.set_material(p.Ms_cells(), p.A_cells(), p.Ku_cells(), p.axis, p.alpha, p.gamma)
+        h_one = me1.h_eff(p.m0, oracle_mod.DEMAG)
+    finally:
+        oracle_mod.set_num_threads(all_threads)
+    assert np.array_equal(h_all, h_one)
