@@ -11,31 +11,7 @@ import numpy as np
 import pytest
 
 import nm_inputs as inp
-
-
-def aharoni_Dz(a, b, c):
-    """Demagnetising factor along c of a prism with half-sides a, b, c (Aharoni 1998)."""
-    abc = math.sqrt(a * a + b * b + c * c)
-    ab = math.sqrt(a * a + b * b)
-    bc = math.sqrt(b * b + c * c)
-    ac = math.sqrt(a * a + c * c)
-    t = ((b * b - c * c) / (2 * b * c) * math.log((abc - a) / (abc + a))
-         + (a * a - c * c) / (2 * a * c) * math.log((abc - b) / (abc + b))
-         + b / (2 * c) * math.log((ab + a) / (ab - a))
-         + a / (2 * c) * math.log((ab + b) / (ab - b))
-         + c / (2 * a) * math.log((bc - b) / (bc + b))
-         + c / (2 * b) * math.log((ac - a) / (ac + a))
-         + 2 * math.atan(a * b / (c * abc))
-         + (a ** 3 + b ** 3 - 2 * c ** 3) / (3 * a * b * c)
-         + (a * a + b * b - 2 * c * c) / (3 * a * b * c) * abc
-         + c / (a * b) * (ac + bc)
-         - (ab ** 3 + bc ** 3 + ac ** 3) / (3 * a * b * c))
-    return t / math.pi
-
-
-def aharoni_factors(L):
-    hx, hy, hz = L[0] / 2, L[1] / 2, L[2] / 2
-    return np.array([aharoni_Dz(hy, hz, hx), aharoni_Dz(hz, hx, hy), aharoni_Dz(hx, hy, hz)])
+from helpers import aharoni_Dz, aharoni_factors
 
 
 def test_aharoni_reference_is_consistent():
