@@ -81,8 +81,10 @@ typedef struct nm_mesh_s *nm_mesh;
 
 /* Create a mesh of n1 x n2 x n3 cells of size dx1 x dx2 x dx3 (metres), precision NM_F32 or NM_F64,
  * working on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
- * Allocates every device workspace the mesh needs.  Errors: NM_ERR_ARG (n_k < 1, dx_k <= 0, bad
- * precision, out == NULL), NM_ERR_OOM, NM_ERR_CUDA. */
+ * Supported sizes: 1 <= n1, n2 <= 1024 and 1 <= n3 <= 64 (padded transform lengths up to 2048 along x
+ * and y and 128 along z); nm_footprint_bytes gives the device memory a size takes.
+ * Allocates every device workspace the mesh needs.  Errors: NM_ERR_ARG (n_k < 1, a size beyond the
+ * supported range, dx_k <= 0, bad precision, out == NULL), NM_ERR_OOM, NM_ERR_CUDA. */
 int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision,
                    void *cuda_stream, nm_mesh *out);
 

@@ -33,9 +33,11 @@ def _heff_gpu(nmgb, p, precision, m, terms, t=0.0):
     return h
 
 
-# N3 = 2..32 covers every z transform length up to 64 (P3 = 4, 8, 16, 32, 64), full and ragged
+# N3 = 2..64 covers every z transform length (P3 = 4, 8, 16, 32, 64 in registers for FP32, 128 through
+# shared memory), full and ragged, up to the largest supported N3
 SHAPES = [(1, 1, 1), (2, 1, 1), (3, 2, 1), (5, 3, 2), (7, 1, 3), (4, 6, 1), (13, 7, 5), (16, 16, 4), (9, 11, 3),
-          (1, 5, 4), (6, 5, 9), (3, 4, 16), (3, 4, 20), (2, 3, 32)]
+          (1, 5, 4), (6, 5, 9), (3, 4, 16), (3, 4, 20), (2, 3, 32), (2, 3, 33), (5, 4, 48), (3, 2, 64),
+          (1, 1, 64)]
 
 
 @pytest.mark.parametrize("precision", [1, 0])
