@@ -91,10 +91,13 @@ int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, i
 /* As nm_create_mesh, with the nodal basis chosen (section "Low-Dimensional Geometries"): basis 3 is the
  * trilinear basis of nm_create_mesh, (n1+1) x (n2+1) x (n3+1) nodes; basis 2 is the 2D nodal basis with
  * full 3D integration, (n1+1) x (n2+1) x 1 nodes whose basis functions are constant along z over all n3
- * cell layers (thin films: half the degrees of freedom of one cell layer).  Every nodal field of a
- * basis-2 mesh has shape (n1+1, n2+1, 1, 3); cell fields keep all n3 layers.  The transpose product and
- * both adjoints (nm_h_eff_vjp, nm_adjoint_run, nm_adjoint_continuous) need basis 3 and return
- * NM_ERR_ARG on a basis-2 mesh.  Errors: as nm_create_mesh; NM_ERR_ARG for a basis other than 2 or 3. */
+ * cell layers (thin films: half the degrees of freedom of one cell layer); basis 1 is the 1D nodal basis
+ * with full 3D integration, (n1+1) x 1 x 1 nodes whose basis functions are constant along y and z over
+ * all n2 x n3 cells of the cross-section (wires).  Every nodal field of a basis-2 (basis-1) mesh has
+ * shape (n1+1, n2+1, 1, 3) ((n1+1, 1, 1, 3)); cell fields keep all n2 x n3 cells.  The transpose product,
+ * both adjoints (nm_h_eff_vjp, nm_adjoint_run, nm_adjoint_continuous) and the DMI term need basis 3 and
+ * return NM_ERR_ARG on other meshes.  Errors: as nm_create_mesh; NM_ERR_ARG for a basis other than 1, 2
+ * or 3. */
 int nm_create_mesh_basis(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, int basis,
                          void *cuda_stream, nm_mesh *out);
 
@@ -143,7 +146,7 @@ int nm_set_terms(nm_mesh mesh, unsigned terms);
  * its variation is assembled cell by cell from the element integrals int phi_i d_k phi_i' (k = x, y) of
  * the trilinear basis, like the exchange (Eqs. weak_form_impl_f, weak_form_impl), over magnetic cells,
  * and divided by the lumped mass.  Needs the 3D basis.  Errors: NM_ERR_ARG (non-finite values, a
- * basis-2 mesh), NM_ERR_OOM, NM_ERR_CUDA. */
+ * mesh of basis 1 or 2), NM_ERR_OOM, NM_ERR_CUDA. */
 int nm_set_dmi(nm_mesh mesh, const double *D, double D0);
 
 /* One integrator step on the resident state.  NM_RK4 uses *dt as the fixed step; NM_DP54 attempts

@@ -159,7 +159,8 @@ class Mesh:
 
     def __init__(self, n, dx, precision=F32, stream=None, basis=3):
         """basis 3: trilinear nodal basis; basis 2: nodal basis constant along z over all cell layers
-        (nodes (N1+1, N2+1, 1), section "Low-Dimensional Geometries")."""
+        (nodes (N1+1, N2+1, 1)); basis 1: nodal basis constant along y and z over the whole cross-section
+        (nodes (N1+1, 1, 1)); section "Low-Dimensional Geometries"."""
         import torch
         if not torch.cuda.is_available():
             raise NMError(ERR_CUDA, "no CUDA device: this library has no CPU path")
@@ -169,7 +170,7 @@ class Mesh:
         self.dx = tuple(float(v) for v in dx)
         self.precision = int(precision)
         self.basis = int(basis)
-        self.nodes = (self.n[0] + 1, self.n[1] + 1, 1 if self.basis == 2 else self.n[2] + 1)
+        self.nodes = (self.n[0] + 1, 1 if self.basis == 1 else self.n[1] + 1, self.n[2] + 1 if self.basis == 3 else 1)
         self.dtype = torch.float64 if self.precision == F64 else torch.float32
         self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream

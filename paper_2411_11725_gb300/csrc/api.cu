@@ -43,8 +43,9 @@ static Geom make_geom(int n1, int n2, int n3, int basis = 3)
     Geom g{};
     g.N1 = n1; g.N2 = n2; g.N3 = n3;
     g.basis = basis;
-    g.nn1 = n1 + 1; g.nn2 = n2 + 1; g.nn3 = basis == 2 ? 1 : n3 + 1;
-    g.zsn = basis == 2 ? 0 : g.nn1 * g.nn2;
+    g.nn1 = n1 + 1; g.nn2 = basis == 1 ? 1 : n2 + 1; g.nn3 = basis == 3 ? n3 + 1 : 1;
+    g.zsn = basis == 3 ? g.nn1 * g.nn2 : 0;
+    g.ysn = basis == 1 ? 0 : g.nn1;
     g.n_nodes = (long)g.nn1 * g.nn2 * g.nn3;
     g.n_cells = (long)n1 * n2 * n3;
     g.ns = round_up(g.n_nodes, 64);
@@ -183,9 +184,10 @@ extern "C" int nm_create_mesh_basis(int n1, int n2, int n3, double dx1, double d
                                     int basis, void *cuda_stream, nm_mesh *out)
 {
     g_last_error.clear();
-    if (basis != 2 && basis != 3) {
+    if (basis < 1 || basis > 3) {
         if (out) *out = nullptr;
-        return fail(NM_ERR_ARG, "basis must be 3 (trilinear) or 2 (constant along z), got %d", basis);
+        return fail(NM_ERR_ARG, "basis must be 3 (trilinear), 2 (constant along z) or 1 (constant along y and z), got %d",
+                    basis);
     }
     return create_mesh(n1, n2, n3, dx1, dx2, dx3, precision, cuda_stream, nullptr, out, basis);
 }

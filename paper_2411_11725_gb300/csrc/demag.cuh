@@ -9,10 +9,12 @@ namespace nm {
 
 struct Geom {
     int N1, N2, N3;            // cells
-    int nn1, nn2, nn3;         // nodes = cells + 1 (nn3 = 1 with the 2D basis)
+    int nn1, nn2, nn3;         // nodes = cells + 1 (nn3 = 1 with the 2D basis, nn2 = nn3 = 1 with the 1D)
     int basis;                 // 3: trilinear nodal basis; 2: 2D nodal basis, constant along z over all N3
-                               // cell layers (section "Low-Dimensional Geometries")
-    int zsn;                   // node offset between the z corners of a cell: nn1 nn2 (3D) or 0 (2D)
+                               // cell layers; 1: 1D nodal basis, constant along y and z over the whole
+                               // cross-section (section "Low-Dimensional Geometries")
+    int zsn;                   // node offset between the z corners of a cell: nn1 nn2 (3D) or 0 (2D, 1D)
+    int ysn;                   // node offset between the y corners of a cell: nn1 (3D, 2D) or 0 (1D)
     long n_nodes, n_cells;
     long ns;                   // component stride of nodal SoA arrays
     long cs;                   // component stride of cell SoA arrays

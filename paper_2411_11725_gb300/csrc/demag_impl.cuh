@@ -120,24 +120,25 @@ __device__ __forceinline__ XInfo x_info(const Geom &g, const FastDiv &nrf, int L
     const int yy = row - zz * g.N2;
     XInfo x;
     x.cell = row * g.N1;
-    x.in = cell_in ? c * (int)g.cs + x.cell : c * (int)g.ns + zz * g.zsn + yy * g.nn1;
+    x.in = cell_in ? c * (int)g.cs + x.cell : c * (int)g.ns + zz * g.zsn + yy * g.ysn;
     x.spec = c * (int)g.s_comp + (zz * g.P2 + yy) * g.Xp;
     return x;
 }
 
 // M of the cell pair (x, x+1) of a row: M_c = Ms_c * (1/8) sum_{i in {0,1}^3} y_{c+i}.  p points at node
-// (x, yy, zz) of one component; `plane` is the node offset of the upper z corners (0 with the 2D basis,
-// where the 8-corner mean is the mean of the 4 in-plane corners).
+// (x, yy, zz) of one component; `row` is the node offset of the upper y corners (0 with the 1D basis) and
+// `plane` that of the upper z corners (0 with the 2D and 1D bases, where the 8-corner mean is the mean of
+// the 4 in-plane corners, or of the 2 corners along x).
 template <typename T>
-__device__ __forceinline__ Cx<T> cell_M_pair(const T *__restrict__ p, int nn1, int plane, const T *__restrict__ Ms,
+__device__ __forceinline__ Cx<T> cell_M_pair(const T *__restrict__ p, int row, int plane, const T *__restrict__ Ms,
                                              T Ms0, int cell, bool has2)
 {
-    const T a0 = (p[0] + p[nn1]) + (p[plane] + p[plane + nn1]);
-    const T a1 = (p[1] + p[nn1 + 1]) + (p[plane + 1] + p[plane + nn1 + 1]);
+    const T a0 = (p[0] + p[row]) + (p[plane] + p[plane + row]);
+    const T a1 = (p[1] + p[row + 1]) + (p[plane + 1] + p[plane + row + 1]);
     const T ms0 = Ms ? Ms[cell] : Ms0;
     T m0 = ms0 * T(0.125) * (a0 + a1), m1 = T(0);
     if (has2) {
-        const T a2 = (p[2] + p[nn1 + 2]) + (p[plane + 2] + p[plane + nn1 + 2]);
+        const T a2 = (p[2] + p[row + 2]) + (p[plane + 2] + p[plane + row + 2]);
         const T ms1 = Ms ? Ms[cell + 1] : Ms0;
         m1 = ms1 * T(0.125) * (a1 + a2);
     }
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 8 : 4)
     if (nl <= 0) return;
     if (threadIdx.x < nl) info[threadIdx.x] = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), l0 + threadIdx.x, CELL_IN);
     __syncthreads();
-    const int N1 = g.N1, nn1 = g.nn1, plane = g.zsn;  // 2D basis: both z corners are the node itself
+    const int N1 = g.N1, row = g.ysn, plane = g.zsn;  // 2D (1D) basis: both z (y and z) corners are the node
     const T *Ms = b.Ms;
     const T Ms0 = b.Ms0;
     auto src = [&](int l, int i) -> Cx<T> {
@@ -169,7 +170,7 @@ __global__ void __launch_bounds__(kXThreads, sizeof(T) == 4 ? 8 : 4)
         const XInfo xi = info[l];
         const T *p = in + xi.in + x;
         if (CELL_IN) return cx<T>(p[0], x + 1 < N1 ? p[1] : T(0));
-        return cell_M_pair<T>(p, nn1, plane, Ms, Ms0, xi.cell + x, x + 1 < N1);
+        return cell_M_pair<T>(p, row, plane, Ms, Ms0, xi.cell + x, x + 1 < N1);
     };
     f3::fft<T, LG, -1, false, false, true, kXEpt<T, LG>>(buf, nl, FastDiv(1u), b.tw, g.twlg, (N1 + 1) >> 1, Q, src,
                                                          f3::NoFn<T>());
@@ -214,7 +215,7 @@ __global__ void k_x_fwd1(Geom g, DemagBufs<T> b, const T *__restrict__ in)
     const XInfo xi = x_info(g, FastDiv((unsigned)(g.N2 * g.N3)), L, CELL_IN);
     T v;
     if (CELL_IN) v = in[xi.in];
-    else v = cell_M_pair<T>(in + xi.in, g.nn1, g.zsn, b.Ms, b.Ms0, xi.cell, false).x;
+    else v = cell_M_pair<T>(in + xi.in, g.ysn, g.zsn, b.Ms, b.Ms0, xi.cell, false).x;
     b.S[xi.spec] = cx<T>(v, T(0));
 }
 

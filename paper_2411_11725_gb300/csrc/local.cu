@@ -568,6 +568,157 @@ __global__ void __launch_bounds__(256) k_node2d(LocalParams<T> p, const T *__res
     }
 }
 
+// 1D basis (section "Low-Dimensional Geometries"): nodes along x only; the basis function of node n1 is
+// the hat function of x, constant over the whole N2 x N3 cross-section, so it couples to n1 - 1 and
+// n1 + 1 through the cells of the slab between them (c1 = n1 - 1 on the left, c1 = n1 on the right).
+// With per-cell pattern integrals Wex1, Wm1 (d = |o1|) and slab sums S_o of A, K_o of Ku over magnetic
+// cells,
+//   dE_ex = sum_{o = -1, 1} Wex1[1] S_o (m_{n+o} - m_n),
+//   dE_an = -2 e [Wm1[0] (K_-1 + K_1) (e . m_n) + sum_{o = -1, 1} Wm1[1] K_o (e . m_{n+o})],
+// and the cell->node average takes Ms_c H_c over the cells of both slabs with weight mu0 V/2.  One block
+// per node: its threads sum the slab cells in a fixed order and tree, thread 0 finishes the node.
+constexpr int kNode1dThreads = 128;
+
+template <typename T, bool STAGE>
+__global__ void __launch_bounds__(kNode1dThreads) k_node1d(LocalParams<T> p, const T *__restrict__ y,
+                                                           T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
+                                                           double t_heff)
+{
+    if (STAGE && sa.ctl && sa.ctl->done) return;
+    const Geom &g = p.g;
+    const int n1 = blockIdx.x;
+    // v: slab sums of A (left, right), of Ku (left, right), of Ms_c H_c (3) and of Ms_c h_c (3)
+    constexpr int NV = 10;
+    T v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = T(0);
+    const bool demag = p.MsH && (p.terms & NM_DEMAG), zee_c = p.Msh && (p.terms & NM_ZEE);
+    const long cs = g.cs;
+    const int ncs = g.N2 * g.N3;
+    for (int s = 0; s < 2; ++s) {
+        const int c1 = n1 - 1 + s;
+        if (c1 < 0 || c1 >= g.N1) continue;
+        for (int j = threadIdx.x; j < ncs; j += blockDim.x) {
+            const long c = (long)j * g.N1 + c1;  // cell (c1, j mod N2, j div N2)
+            const T Ms = p.Ms ? p.Ms[c] : p.Ms0;
+            if (!(Ms > T(0))) continue;
+            if (p.terms & NM_EXCH) v[s] += p.A ? p.A[c] : p.A0;
+            if (p.terms & NM_ANIS) v[2 + s] += p.Ku ? p.Ku[c] : p.Ku0;
+            if (demag) {
+                v[4] += p.MsH[c];
+                v[5] += p.MsH[cs + c];
+                v[6] += p.MsH[2 * cs + c];
+            }
+            if (zee_c) {
+                v[7] += p.Msh[c];
+                v[8] += p.Msh[cs + c];
+                v[9] += p.Msh[2 * cs + c];
+            }
+        }
+    }
+    __shared__ T red[kNode1dThreads / 32][NV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T x = v[i];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[w][i] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T x = T(0);
+        for (int k = 0; k < kNode1dThreads / 32; ++k) x += red[k][i];
+        v[i] = x;
+    }
+    const int ns = (int)g.ns, n = n1;
+    const double t = STAGE ? (sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed) : t_heff;
+    const T im = p.inv_mass[n];
+    const bool magnetic = im > T(0);
+    const T mx = y[n], my = y[ns + n], mz = y[2 * ns + n];
+    T ex = 0, ey = 0, ez = 0;
+    T pe = p.Wm1[0] * (v[2] + v[3]) * (p.e0 * mx + p.e1 * my + p.e2 * mz);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        const int q = s == 0 ? n1 - 1 : n1 + 1;
+        if (q < 0 || q >= g.nn1) continue;  // (its slab does not exist)
+        const T qx = y[q], qy = y[ns + q], qz = y[2 * ns + q];
+        const T wq = p.Wex1[1] * v[s];
+        ex += wq * (qx - mx);
+        ey += wq * (qy - my);
+        ez += wq * (qz - mz);
+        pe += p.Wm1[1] * v[2 + s] * (p.e0 * qx + p.e1 * qy + p.e2 * qz);
+    }
+    T hx = -ex + T(2) * p.e0 * pe, hy = -ey + T(2) * p.e1 * pe, hz = -ez + T(2) * p.e2 * pe;
+    T cx = v[4], cy = v[5], cz = v[6];
+    if (zee_c) {
+        const T sc = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
+        cx += sc * v[7];
+        cy += sc * v[8];
+        cz += sc * v[9];
+    }
+    if (p.raw) {
+        hx += p.mu0V2 * cx;
+        hy += p.mu0V2 * cy;
+        hz += p.mu0V2 * cz;
+    } else {
+        hx = im * (hx + p.mu0V2 * cx);
+        hy = im * (hy + p.mu0V2 * cy);
+        hz = im * (hz + p.mu0V2 * cz);
+        if (magnetic && (p.terms & NM_ZEE)) {
+            const T su = (T)time_factor<T>(p.hu_freq, p.hu_phase, t);
+            hx += (T)p.hu0 * su;
+            hy += (T)p.hu1 * su;
+            hz += (T)p.hu2 * su;
+        }
+    }
+    if (!STAGE) {
+        out[n] = hx;
+        out[ns + n] = hy;
+        out[2 * ns + n] = hz;
+        return;
+    }
+    T kx = 0, ky = 0, kz = 0;
+    if (magnetic) {
+        const T ax = my * hz - mz * hy, ay = mz * hx - mx * hz, az = mx * hy - my * hx;
+        const T bx = my * az - mz * ay, by = mz * ax - mx * az, bz = mx * ay - my * ax;
+        kx = -p.gam_t * (ax + p.alpha_t * bx);
+        ky = -p.gam_t * (ay + p.alpha_t * by);
+        kz = -p.gam_t * (az + p.alpha_t * bz);
+    }
+    out[n] = kx;
+    out[ns + n] = ky;
+    out[2 * ns + n] = kz;
+    if (y_next) {
+        T px = 0, py = 0, pz = 0;
+        for (int j = 0; j + 1 < sa.s && j < 7; ++j) {
+            const T aj = sizeof(T) == 4 ? (T)sa.af[j] : (T)sa.a[j];
+            if (aj == T(0)) continue;
+            const T *kj = (const T *)sa.k[j];
+            px += aj * kj[n];
+            py += aj * kj[ns + n];
+            pz += aj * kj[2 * ns + n];
+        }
+        const T as = sizeof(T) == 4 ? (T)sa.af_s : (T)sa.a_s;
+        px += as * kx;
+        py += as * ky;
+        pz += as * kz;
+        const double dt = sa.ctl ? sa.ctl->dt : 0.0;
+        if (sizeof(T) == 4 && sa.mf) {
+            const float dtf = (float)dt;
+            y_next[n] = (T)(sa.mf[n] + dtf * (float)px);
+            y_next[ns + n] = (T)(sa.mf[ns + n] + dtf * (float)py);
+            y_next[2 * ns + n] = (T)(sa.mf[2 * ns + n] + dtf * (float)pz);
+        } else {
+            y_next[n] = (T)(sa.m[n] + dt * (double)px);
+            y_next[ns + n] = (T)(sa.m[ns + n] + dt * (double)py);
+            y_next[2 * ns + n] = (T)(sa.m[2 * ns + n] + dt * (double)pz);
+        }
+    }
+}
+
 // Interfacial DMI, E = int D [m_z div m - (m . grad) m_z] (a reading of the paper's "antisymmetric
 // exchange"), assembled like the exchange: with G_k(i,i') = int_cell phi_i d_k phi_i' and its
 // antisymmetric part A_k, node n couples to n + o through every magnetic cell holding both nodes,
@@ -646,6 +797,10 @@ void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaSt
                                                                                           StageArgs{}, t);
         return;
     }
+    if (p.g.basis == 1) {
+        k_node1d<T, false><<<p.g.nn1, kNode1dThreads, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t);
+        return;
+    }
     int zc;
     const dim3 grid = node_grid<T>(p.g, &zc);
     if (p.hdmi) {
@@ -662,6 +817,10 @@ void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, 
     if (p.g.basis == 2) {
         k_node2d<T, true><<<dim3(div_up(p.g.nn1, 32), div_up(p.g.nn2, 8)), 256, 0, st>>>(p, y, k_out, y_next, sa,
                                                                                          0.0);
+        return;
+    }
+    if (p.g.basis == 1) {
+        k_node1d<T, true><<<p.g.nn1, kNode1dThreads, 0, st>>>(p, y, k_out, y_next, sa, 0.0);
         return;
     }
     int zc;
@@ -693,6 +852,13 @@ __global__ void k_mass(Geom g, const double *__restrict__ Ms, double Ms0, double
             const int c1 = n1 - ((i >> 1) & 1), c2 = n2 - (i & 1);
             if (c1 < 0 || c1 >= g.N1 || c2 < 0 || c2 >= g.N2) continue;
             for (int c3 = 0; c3 < g.N3; ++c3) s += 2.0 * (Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0);
+        }
+    } else if (g.basis == 1) {
+        // the 1D basis function is constant over the cross-section: every cell of the two slabs beside
+        // the node holds it, each with integral V/2 (four times the 3D corner share)
+        for (int c1 = n1 - 1; c1 <= n1; ++c1) {
+            if (c1 < 0 || c1 >= g.N1) continue;
+            for (long j = 0; j < (long)g.N2 * g.N3; ++j) s += 4.0 * (Ms ? Ms[j * g.N1 + c1] : Ms0);
         }
     } else {
         for (int i = 0; i < 8; ++i) {

@@ -186,6 +186,12 @@ inline LocalParams<T> local_params(nm_mesh M, unsigned terms)
         p.Wex2[d] = (T)(2.0 * (K1x * M1y + M1x * K1y) * dx[2]);
         p.Wm2[d] = (T)(M1x * M1y * dx[2]);
     }
+    p.mu0V2 = (T)(kMu0 * V / 2.0);
+    for (int d = 0; d < 2; ++d) {
+        const double M1x = dx[0] * (d ? 1.0 / 6.0 : 1.0 / 3.0), K1x = (d ? -1.0 : 1.0) / dx[0];
+        p.Wex1[d] = (T)(2.0 * K1x * dx[1] * dx[2]);
+        p.Wm1[d] = (T)(M1x * dx[1] * dx[2]);
+    }
     p.A = (const T *)M->A_d;
     p.Ku = (const T *)M->Ku_d;
     p.Ms = (const T *)M->Ms_d;

@@ -573,7 +573,7 @@ __global__ void k_convert(long n, const Tin *__restrict__ a, Tout *__restrict__ 
 }
 
 // volume weights of the nodal mean: sum over adjacent magnetic cells of V/8 (V/4 per in-plane cell and
-// layer with the 2D basis)
+// layer with the 2D basis, V/2 per cell of the two slabs beside the node with the 1D basis)
 template <typename T>
 __global__ void k_node_volume(Geom g, const double *__restrict__ Ms, double Ms0, double V8, T *vol)
 {
@@ -590,6 +590,12 @@ __global__ void k_node_volume(Geom g, const double *__restrict__ Ms, double Ms0,
             if (c1 < 0 || c1 >= g.N1 || c2 < 0 || c2 >= g.N2) continue;
             for (int c3 = 0; c3 < g.N3; ++c3)
                 if ((Ms ? Ms[((long)c3 * g.N2 + c2) * g.N1 + c1] : Ms0) > 0.0) s += 2.0 * V8;
+        }
+    } else if (g.basis == 1) {  // 1D basis: every cell of the two slabs beside the node, V/2 each
+        for (int c1 = n1 - 1; c1 <= n1; ++c1) {
+            if (c1 < 0 || c1 >= g.N1) continue;
+            for (long j = 0; j < (long)g.N2 * g.N3; ++j)
+                if ((Ms ? Ms[j * g.N1 + c1] : Ms0) > 0.0) s += 4.0 * V8;
         }
     } else {
         for (int i = 0; i < 8; ++i) {

@@ -49,6 +49,10 @@ def test_host_side_validation(lib):
     assert lib.nm_create_mesh(4, 4, 4, 1e-9, 1e-9, 1e-9, 7, None, ctypes.byref(h)) == -1
     assert lib.nm_create_mesh(4, 4, 4, 1e-9, 1e-9, 1e-9, 0, None, None) == -1
     assert lib.nm_create_mesh(4096, 4, 4, 1e-9, 1e-9, 1e-9, 0, None, ctypes.byref(h)) == -1
+    for basis in (0, 4):
+        assert lib.nm_create_mesh_basis(4, 4, 4, 1e-9, 1e-9, 1e-9, 0, basis, None, ctypes.byref(h)) == -1
+        assert b"basis must be" in lib.nm_last_error()
+    assert lib.nm_create_mesh_basis(0, 1, 1, 1e-9, 1e-9, 1e-9, 0, 1, None, ctypes.byref(h)) == -1
     assert lib.nm_destroy_mesh(None) == 0
     assert lib.nm_set_terms(None, 1) == -1
     assert lib.nm_sync(None) == -1
