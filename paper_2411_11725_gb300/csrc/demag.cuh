@@ -14,7 +14,6 @@ struct Geom {
                                // cell layers; 1: 1D nodal basis, constant along y and z over the whole
                                // cross-section (section "Low-Dimensional Geometries")
     int zsn;                   // node offset between the z corners of a cell: nn1 nn2 (3D) or 0 (2D, 1D)
-    int ysn;                   // node offset between the y corners of a cell: nn1 (3D, 2D) or 0 (1D)
     long n_nodes, n_cells;
     long ns;                   // component stride of nodal SoA arrays
     long cs;                   // component stride of cell SoA arrays
@@ -26,6 +25,7 @@ struct Geom {
     long s_comp;               // component stride of the spectrum buffer = N3 * P2 * Xp
     long t_comp;               // component stride of the tensor spectrum = H3 * H2 * Xp
     FastDiv n2f;               // division by N2 (cell row -> (y, z))
+    int ysn;                   // node offset between the y corners of a cell: nn1 (3D, 2D) or 0 (1D)
 };
 
 template <typename T>

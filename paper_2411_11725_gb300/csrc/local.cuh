@@ -24,9 +24,6 @@ struct LocalParams {
     // 2D basis (section "Low-Dimensional Geometries"): the in-plane pattern integrals per cell layer
     // (pattern d = 2 |o1| + |o2|), through the layer's thickness, and mu0 V / 4
     T Wex2[4], Wm2[4], mu0V4;
-    // 1D basis: the pattern integrals along x (d = |o1|) per cell of the cross-section, through its
-    // area, and mu0 V / 2
-    T Wex1[2], Wm1[2], mu0V2;
     // interfacial DMI: raw field buffer (NULL: term off), cell map or uniform value, and the pattern
     // weights of the antisymmetric element integrals (dmx by (|o2|,|o3|), dmy by (|o1|,|o3|))
     T *hdmi;
@@ -46,6 +43,10 @@ struct LocalParams {
     T gam_t, alpha_t;  // the same in the working precision
     int raw;           // 1: output -dE (no division by the mass, no uniform applied field)
     double alpha;
+    // 1D basis: the pattern integrals along x (d = |o1|) per cell of the cross-section, through its
+    // area, and mu0 V / 2 (last, so that the fields above keep the offsets the other kernels were tuned
+    // with)
+    T Wex1[2], Wm1[2], mu0V2;
 };
 
 // What the node kernel writes.
