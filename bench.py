@@ -416,12 +416,16 @@ def run_ours(args, rank, world, dist):
     serving = None
     if args.serve_requests > 0:
         serving = run_serving(args.serve_requests, int(args.serve_budget_gb * (1 << 30)), args.serve_max_active)
-    film = None
+    film = wire = None
     if args.film_steps > 0 and rank == 0:
         try:
             film = run_film(nmgb, args.film_steps)
         except Exception as e:  # a side measurement: report it, keep the headline line
             film = {"error": f"{type(e).__name__}: {e}"}
+        try:
+            wire = run_wire(nmgb, args.film_steps)
+        except Exception as e:
+            wire = {"error": f"{type(e).__name__}: {e}"}
     gradients = None
     if args.grad_steps > 0 and rank == 0:
         try:
@@ -464,6 +468,7 @@ def run_ours(args, rank, world, dist):
         "serving": serving,
         "gradients": gradients,
         "thin_film_2d_basis": film,
+        "wire_1d_basis": wire,
         "clocks": clocks,
         "gpu_launches": int(launches_per_step * K),
     }
@@ -475,11 +480,28 @@ def run_film(nmgb, n_steps, grid=(1024, 1024, 1)):
     the trilinear basis (2 node layers) and with the 2D basis (1 node layer, section "Low-Dimensional
     Geometries"): wall time per step (graph replays, synchronised) and node-steps/s of each."""
     p = inp.throughput(grid, seed=5, with_m0=False)
-    dx = (p.dx[0], p.dx[1], 1e-9)
-    rng = np.random.default_rng(5)
-    out = {"workload": f"film {grid[0]}x{grid[1]}x{grid[2]} cells of 3x3x1 nm, throughput material, FP32 "
-                       f"field, DP5(4) rtol=atol=1e-5, random unit m0, {n_steps} timed steps"}
-    for basis in (3, 2):
+    out = run_bases(nmgb, n_steps, p, (p.dx[0], p.dx[1], 1e-9), (3, 2), 5,
+                    f"film {grid[0]}x{grid[1]}x{grid[2]} cells of 3x3x1 nm")
+    out["step_time_ratio_3d_over_2d"] = out["basis3"]["ms_per_step"] / out["basis2"]["ms_per_step"]
+    return out
+
+
+def run_wire(nmgb, n_steps, grid=(1024, 4, 4)):
+    """A wire of 4 x 4 cells across (3 nm cells of the throughput material), FP32 DP5(4) steps with the
+    trilinear basis (5 x 5 nodes across) and with the 1D basis (one node per position along the wire,
+    section "Low-Dimensional Geometries"): wall time per step and node-steps/s of each."""
+    p = inp.throughput(grid, seed=6, with_m0=False)
+    out = run_bases(nmgb, n_steps, p, p.dx, (3, 1), 6, f"wire {grid[0]}x{grid[1]}x{grid[2]} cells of 3 nm")
+    out["step_time_ratio_3d_over_1d"] = out["basis3"]["ms_per_step"] / out["basis1"]["ms_per_step"]
+    return out
+
+
+def run_bases(nmgb, n_steps, p, dx, bases, seed, what):
+    """FP32 DP5(4) steps of the problem p on cells dx with each nodal basis in `bases`."""
+    rng = np.random.default_rng(seed)
+    out = {"workload": f"{what}, throughput material, FP32 field, DP5(4) rtol=atol=1e-5, random unit m0, "
+                       f"{n_steps} timed steps"}
+    for basis in bases:
         me = nmgb.Mesh(p.n, dx, nmgb.F32, basis=basis)
         me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
         me.set_terms(p.terms)
@@ -497,7 +519,6 @@ def run_film(nmgb, n_steps, grid=(1024, 1024, 1)):
         out[f"basis{basis}"] = {"nodes": nn, "ms_per_step": ms / max(1, (a1 - a0) + (r1 - r0)),
                                 "node_steps_per_s": nn * (a1 - a0) / (ms * 1e-3)}
         me.close()
-    out["step_time_ratio_3d_over_2d"] = out["basis3"]["ms_per_step"] / out["basis2"]["ms_per_step"]
     return out
 
 
@@ -622,7 +643,7 @@ def main():
     ap.add_argument("--serve-budget-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-active", type=int, default=16)
     ap.add_argument("--grad-steps", type=int, default=16, help="RK4 steps of the gradient timing leg (0: skip)")
-    ap.add_argument("--film-steps", type=int, default=10, help="DP5 steps of the 2D-basis film leg (0: skip)")
+    ap.add_argument("--film-steps", type=int, default=10, help="DP5 steps of the 2D-basis film and 1D-basis wire legs (0: skip)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
