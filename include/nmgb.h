@@ -94,10 +94,11 @@ int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, i
  * cell layers (thin films: half the degrees of freedom of one cell layer); basis 1 is the 1D nodal basis
  * with full 3D integration, (n1+1) x 1 x 1 nodes whose basis functions are constant along y and z over
  * all n2 x n3 cells of the cross-section (wires).  Every nodal field of a basis-2 (basis-1) mesh has
- * shape (n1+1, n2+1, 1, 3) ((n1+1, 1, 1, 3)); cell fields keep all n2 x n3 cells.  The transpose product,
- * both adjoints (nm_h_eff_vjp, nm_adjoint_run, nm_adjoint_continuous) and the DMI term need basis 3 and
- * return NM_ERR_ARG on other meshes.  Errors: as nm_create_mesh; NM_ERR_ARG for a basis other than 1, 2
- * or 3. */
+ * shape (n1+1, n2+1, 1, 3) ((n1+1, 1, 1, 3)); cell fields keep all n2 x n3 cells.  The transpose product
+ * and both adjoints (nm_h_eff_vjp, nm_adjoint_run, nm_adjoint_continuous) work on every basis: the
+ * low-dimensional system is the trilinear one restricted to m constant along z (or y and z), and its
+ * gradients are those of the restricted system.  The DMI term needs basis 3 (NM_ERR_ARG otherwise).
+ * Errors: as nm_create_mesh; NM_ERR_ARG for a basis other than 1, 2 or 3. */
 int nm_create_mesh_basis(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision, int basis,
                          void *cuda_stream, nm_mesh *out);
 

@@ -109,7 +109,6 @@ extern "C" int nm_h_eff_vjp(nm_mesh M, const void *m, const void *v, unsigned te
     if (terms & ~NM_TERMS_MASK) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
     if (!isfinite(t)) return fail(NM_ERR_ARG, "t must be finite");
     if (!M->material_set) return fail(NM_ERR_STATE, "material not set");
-    if (M->g.basis != 3) return fail(NM_ERR_ARG, "the transpose product needs the 3D nodal basis");
     return M->prec == NM_F64 ? heff_vjp_t<double>(M, m, v, terms, t, grad_m, grad_Ms)
                              : heff_vjp_t<float>(M, m, v, terms, t, grad_m, grad_Ms);
 }
@@ -589,7 +588,6 @@ extern "C" int nm_adjoint_run(nm_mesh M, int method, double t_end, double rtol, 
 {
     int rc = check_step_args(M, method, rtol, atol);
     if (rc) return rc;
-    if (M->g.basis != 3) return fail(NM_ERR_ARG, "the adjoint needs the 3D nodal basis");
     if (!weight || !loss) return fail(NM_ERR_ARG, "weight and loss are required");
     if (!isfinite(t_end) || !isfinite(dt0) || !isfinite(sample_dt)) return fail(NM_ERR_ARG, "non-finite argument");
     if (method == NM_RK4 && !(dt0 > 0)) return fail(NM_ERR_ARG, "RK4 needs dt0 > 0");
@@ -799,7 +797,6 @@ extern "C" int nm_adjoint_continuous(nm_mesh M, double t_end, long n_steps, cons
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     if (!M->material_set) return fail(NM_ERR_STATE, "material not set");
     if (!M->state_set) return fail(NM_ERR_STATE, "no resident state");
-    if (M->g.basis != 3) return fail(NM_ERR_ARG, "the adjoint needs the 3D nodal basis");
     if (!weight || !loss) return fail(NM_ERR_ARG, "weight and loss are required");
     if (!isfinite(t_end)) return fail(NM_ERR_ARG, "non-finite argument");
     if (n_steps < 1) return fail(NM_ERR_ARG, "n_steps must be >= 1");

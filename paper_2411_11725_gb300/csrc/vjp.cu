@@ -24,8 +24,10 @@ __global__ void k_cell_moment(Geom g, const T *__restrict__ y, const T *__restri
     const long r = c / g.N1;
     const int c2 = (int)(r % g.N2);
     const int c3 = (int)(r / g.N2);
-    const long n0 = ((long)c3 * g.nn2 + c2) * g.nn1 + c1;
-    const long sy = g.nn1, sz = (long)g.nn1 * g.nn2;
+    // corner offsets of the nodal basis: nn1 and nn1 nn2 for the trilinear basis; 0 along the directions
+    // in which the 2D or 1D basis is constant, where the 8-corner sum counts each node twice (or 4 times)
+    const long sy = g.ysn, sz = g.zsn;
+    const long n0 = (long)c3 * sz + (long)c2 * sy + c1;
     const T ms = Ms ? Ms[c] : Ms0;
     for (int k = 0; k < 3; ++k) {
         const T *p = y + k * g.ns + n0;
@@ -43,8 +45,11 @@ __global__ void k_grad_Ms(Geom g, GradMsArgs a, const T *__restrict__ im, double
     const long r = c / g.N1;
     const int c2 = (int)(r % g.N2);
     const int c3 = (int)(r / g.N2);
-    const long n0 = ((long)c3 * g.nn2 + c2) * g.nn1 + c1;
-    const long sy = g.nn1, sz = (long)g.nn1 * g.nn2;
+    // corner offsets as in k_cell_moment: with the 2D and 1D bases the 8 corners collapse onto the
+    // cell's 4 (2) nodes, which gives the gradient of the restricted system (basis functions that are
+    // sums of trilinear ones, integrals V/4 or V/2 per cell)
+    const long sy = g.ysn, sz = g.zsn;
+    const long n0 = (long)c3 * sz + (long)c2 * sy + c1;
     const long off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
     const T *m = (const T *)a.m, *w = (const T *)a.w, *h = (const T *)a.h;
     double acc = 0.0;

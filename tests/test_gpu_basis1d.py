@@ -117,17 +117,10 @@ def test_wire_dp5_runs_on_one_node_row(nmgb):
     me.close()
 
 
-def test_gradients_and_dmi_need_the_3d_basis(nmgb):
-    import torch
+def test_dmi_needs_the_3d_basis(nmgb):
     rng = np.random.default_rng(18)
     p = inp.random_problem(rng, (4, 2, 1))
     me = _gpu1(nmgb, p, 1)
-    m = _m1(rng, p)
-    me.set_state(m, 0.0, 1e-14)
-    with pytest.raises(nmgb.NMError):
-        me.h_eff_vjp(torch.tensor(m, device="cuda"), torch.tensor(m, device="cuda"))
-    with pytest.raises(nmgb.NMError):
-        me.adjoint_continuous(1e-13, 4, np.ones_like(m))
     with pytest.raises(nmgb.NMError):
         me.set_dmi(1e-3)
     me.close()

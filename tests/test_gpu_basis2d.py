@@ -115,15 +115,10 @@ def test_thin_film_dp5_runs_and_halves_the_nodes(nmgb):
     me.close()
 
 
-def test_gradients_need_the_3d_basis(nmgb):
-    import torch
+def test_dmi_needs_the_3d_basis(nmgb):
     rng = np.random.default_rng(7)
     p = inp.random_problem(rng, (3, 3, 1))
     me = _gpu2(nmgb, p, 1)
-    m = _m2(rng, p)
-    me.set_state(m, 0.0, 1e-14)
     with pytest.raises(nmgb.NMError):
-        me.h_eff_vjp(torch.tensor(m, device="cuda"), torch.tensor(m, device="cuda"))
-    with pytest.raises(nmgb.NMError):
-        me.adjoint_continuous(1e-13, 4, np.ones_like(m))
+        me.set_dmi(1e-3)
     me.close()
