@@ -397,7 +397,10 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
     }
     double *W = nullptr, *tgt = nullptr, *tmp = nullptr;
     ADJ_TRY(galloc((void **)&W, nd3));
-    ADJ_TRY(galloc((void **)&tmp, g.n_nodes * 3 * sizeof(double)));
+    // tmp stages the nodal inputs and outputs and the cell-wise Ms gradient: with the 2D and 1D bases a
+    // mesh can have more cells than nodal values
+    const size_t tmp_bytes = (g.n_nodes * 3 > g.n_cells ? g.n_nodes * 3 : g.n_cells) * sizeof(double);
+    ADJ_TRY(galloc((void **)&tmp, tmp_bytes));
     CUDA_TRY(cudaMemcpyAsync(tmp, weight, g.n_nodes * 3 * sizeof(double), cudaMemcpyHostToDevice, M->st));
     CUDA_TRY(cudaMemsetAsync(W, 0, nd3, M->st));
     launch_aos_to_soa<double, double>(g, tmp, W, M->st);
