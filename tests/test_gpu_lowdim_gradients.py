@@ -139,14 +139,15 @@ def test_discrete_adjoint_matches_finite_differences(nmgb, basis):
     assert abs(fd - ad) <= 1e-5 * abs(fd) + 1e-12 * loss, (fd, ad)
 
 
-@pytest.mark.parametrize("basis", [2, 1])
-def test_continuous_adjoint_converges_to_discrete(nmgb, basis):
+@pytest.mark.parametrize("basis,steps", [(2, (8, 16, 32)), (1, (16, 32, 64))])
+def test_continuous_adjoint_converges_to_discrete(nmgb, basis, steps):
     """The m0, Ms-map and uniform-field gradients of the continuous adjoint approach the discrete
-    adjoint's with the fourth power of the step."""
+    adjoint's with the fourth power of the step.  Each problem is taken over step counts in its
+    asymptotic range (the 1D-basis problem's error constant is larger: 0.38 at 8 steps)."""
     p, W, tgt, m0, _ = _loss_problem(70 + basis, basis)
     T = 2e-12
     errs = {"m0": [], "Ms": [], "h": []}
-    for n in (8, 16, 32):
+    for n in steps:
         me = _gpu(nmgb, p, basis, 1)
         me.set_state(m0, 0.0, 1e-14)
         _, gm, gMs, gh, _ = me.adjoint_continuous(T, n, W, tgt)
