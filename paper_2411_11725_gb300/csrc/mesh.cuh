@@ -16,6 +16,7 @@
 using namespace nm;
 
 int fail(int code, const char *fmt, ...);
+void clear_error();  // every entry point starts with this, so nm_last_error() describes its own failure
 
 #define CUDA_TRY(expr)                                                                                     \
     do {                                                                                                   \
@@ -106,6 +107,8 @@ struct nm_mesh_s {
     std::vector<cudaEvent_t> prof_ev;
     std::vector<const char *> prof_names;
     size_t prof_n = 0;
+    unsigned long long *n_bad_d = nullptr;  // nodes with non-finite values met by nm_set_state (device)
+    int err_f64_terms = 0;  // FP32 meshes: per-node error-norm terms in FP64 (nm_set_error_norm)
 };
 
 

@@ -21,16 +21,53 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 std::mutex g_scratch_mu;
 void *g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // id of the context the address belongs to
 
-// Device address of the scratch array on the current device, looked up once per device (the first
-// call on a device does the look-up).
+// The context id (cuCtxGetId, unique for the life of the process) tells whether the device's primary
+// context is still the one the address was looked up in: after a cudaDeviceReset the module is loaded
+// again and the array may sit elsewhere.  The two driver calls are reached through the runtime's
+// entry-point query, so the library does not link the driver library directly.
+typedef int (*CtxGetCurrentFn)(void **ctx);
+typedef int (*CtxGetIdFn)(void *ctx, unsigned long long *id);
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+std::once_flag g_entry_once;
+
+int current_context_id(unsigned long long *id)
+{
+    std::call_once(g_entry_once, [] {
+        void *f = nullptr, *h = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &h, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess) {
+            g_ctx_get_current = (CtxGetCurrentFn)f;
+            g_ctx_get_id = (CtxGetIdFn)h;
+        }
+        cudaGetLastError();
+    });
+    if (!g_ctx_get_current || !g_ctx_get_id) return fail(NM_ERR_CUDA, "driver context queries unavailable");
+    void *ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != 0 || !ctx) return fail(NM_ERR_CUDA, "no current CUDA context");
+    if (g_ctx_get_id(ctx, id) != 0) return fail(NM_ERR_CUDA, "context id query failed");
+    return NM_OK;
+}
+
+// Device address of the scratch array on the current device, looked up once per device and context
+// (the first call on a device, and the first call after a reset of its primary context, do the
+// look-up).
 int scratch_address(void **out)
 {
     int dev = 0;
     CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(NM_ERR_ARG, "device ordinal %d beyond %d", dev, kMaxDevices);
+    CUDA_TRY(cudaSetDevice(dev));  // makes the device's primary context current on this thread
+    unsigned long long ctx = 0;
+    int rc = current_context_id(&ctx);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_scratch_mu);
-    if (!g_scratch_addr[dev]) {
+    if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
@@ -38,6 +75,7 @@ int scratch_address(void **out)
             return fail(NM_ERR_CUDA, "cudaGetSymbolAddress of the staging array failed: %s", cudaGetErrorString(e));
         }
         g_scratch_addr[dev] = p;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = g_scratch_addr[dev];
     return NM_OK;
@@ -47,6 +85,7 @@ int scratch_address(void **out)
 
 extern "C" int nm_get_state_noalloc(nm_mesh M, double *m_out, double *t, double *dt)
 {
+    clear_error();
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     const Geom &g = M->g;
     const size_t bytes = (size_t)g.n_nodes * 3 * sizeof(double);

@@ -391,6 +391,7 @@ int check_request(const nm_request *q)
 
 extern "C" int nm_server_create(long hbm_budget_bytes, int max_active, nm_server *out)
 {
+    clear_error();
     if (!out) return fail(NM_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (hbm_budget_bytes <= 0) return fail(NM_ERR_ARG, "hbm_budget_bytes must be positive");
@@ -409,6 +410,7 @@ extern "C" int nm_server_create(long hbm_budget_bytes, int max_active, nm_server
 
 extern "C" int nm_server_submit(nm_server S, const nm_request *req)
 {
+    clear_error();
     int rc = check_request(req);
     if (rc) return rc;
     if (!S) return fail(NM_ERR_ARG, "server is NULL");
@@ -431,6 +433,7 @@ extern "C" int nm_server_submit(nm_server S, const nm_request *req)
 
 extern "C" int nm_server_poll(nm_server S, nm_result *out, int max_results, double wait_s, int *n_out)
 {
+    clear_error();
     if (!S || !n_out || (max_results > 0 && !out)) return fail(NM_ERR_ARG, "bad poll arguments");
     if (!(wait_s >= 0) || !isfinite(wait_s)) return fail(NM_ERR_ARG, "wait_s must be finite and >= 0");
     std::unique_lock<std::mutex> lk(S->mu);
@@ -447,6 +450,7 @@ extern "C" int nm_server_poll(nm_server S, nm_result *out, int max_results, doub
 
 extern "C" int nm_server_stats_get(nm_server S, nm_server_stats *out)
 {
+    clear_error();
     if (!S || !out) return fail(NM_ERR_ARG, "bad arguments");
     std::lock_guard<std::mutex> lk(S->mu);
     *out = S->st;
@@ -456,6 +460,7 @@ extern "C" int nm_server_stats_get(nm_server S, nm_server_stats *out)
 
 extern "C" int nm_server_destroy(nm_server S)
 {
+    clear_error();
     if (!S) return NM_OK;
     {
         std::lock_guard<std::mutex> lk(S->mu);
