@@ -121,7 +121,10 @@ int nm_set_field(nm_mesh mesh, int kind, const double *data, const double amp[3]
                  double phase);
 
 /* Resident state for the integrators: m (FP64 nodal vector field, host or device pointer per
- * `where`), time t, next step size dt.  Invalidates the FSAL slope. Errors: NM_ERR_ARG. */
+ * `where`), time t, next step size dt.  Invalidates the FSAL slope.  The layout conversion counts
+ * non-finite components on the device; such a state is refused with NM_ERR_NONFINITE and leaves the
+ * mesh without a state (NM_ERR_STATE from the integrators until a valid state is set).  Synchronises.
+ * Errors: NM_ERR_ARG, NM_ERR_NONFINITE, NM_ERR_CUDA. */
 int nm_set_state(nm_mesh mesh, const double *m, int where, double t, double dt);
 
 /* Copy the resident state out: m_out (FP64 nodal vector field, host or device per `where`; may be
@@ -133,10 +136,21 @@ int nm_get_state(nm_mesh mesh, double *m_out, int where, double *t, double *dt);
  * (default 50). */
 int nm_set_integrator(nm_mesh mesh, int renormalise, double dt_min, int max_rejections);
 
+/* Arithmetic of the per-node terms of the Dormand-Prince error norm on FP32 meshes (the Dormand-Prince
+ * integrator of the time-integration section; the norm and controller of nm_llg_step).  0 (default):
+ * the terms (dt sum_i e_i k_i) / (atol + rtol max(|m|, |m5|)) are formed in FP32 from the FP32 slopes
+ * and the FP32 copy of m, and summed in FP64.  1: every operation of the terms in FP64, from the same
+ * FP32 slopes, the FP64 m and FP64 coefficients.  FP64 meshes always use FP64.  The FP32 terms carry
+ * rounding of about 1e-7 of the largest slope contribution; the slopes themselves carry the FP32 field
+ * error (about 1e-6 relative), so both settings estimate the same error to that accuracy.  GB300's
+ * FP64 rate makes setting 1 several times slower than 0 for this kernel.  Errors: NM_ERR_ARG. */
+int nm_set_error_norm(nm_mesh mesh, int fp64_terms);
+
 /* Effective field h = H_eff(m) at time t for the terms in the mask (NM_EXCH|NM_ANIS|NM_ZEE|NM_DEMAG|NM_DMI):
  * m and h_out are DEVICE pointers to real nodal vector fields; m == NULL uses the resident state.
- * Nodes that touch no magnetic cell get h = 0.  Asynchronous.  Errors: NM_ERR_ARG, NM_ERR_STATE
- * (material not set), NM_ERR_CUDA. */
+ * Nodes that touch no magnetic cell get h = 0.  Asynchronous, so the values of m are not checked: a
+ * non-finite m gives a non-finite h (the demag convolution spreads it over the whole mesh).  Errors:
+ * NM_ERR_ARG, NM_ERR_STATE (material not set), NM_ERR_CUDA. */
 int nm_h_eff(nm_mesh mesh, const void *m, void *h_out, unsigned terms, double t);
 
 /* Select the field terms used by the integrators (default NM_ALL; add NM_DMI for the DMI term). */
@@ -194,7 +208,10 @@ int nm_profile_step(nm_mesh mesh, int method, int reps, double rtol, double atol
  * allocator calls out of its read-back path).  m_out: HOST FP64 nodal vector field (or NULL for t, dt
  * only).  Limit: meshes of at most 174762 nodes (4 MiB / 24 B); larger meshes return NM_ERR_ARG.  The
  * first call on a device looks up the array's device address (cudaGetSymbolAddress); make that first
- * call before any stream capture on that device.  Nothing in the array needs to start at zero.  The
+ * call before any stream capture on that device.  The address is kept per device together with the id
+ * of the context it belongs to: after a reset of the device's primary context (cudaDeviceReset) the
+ * next call looks it up again, so that first call after a reset should also precede any capture.
+ * Nothing in the array needs to start at zero.  The
  * call synchronises the mesh's stream; calls on different meshes that overlap on the GPU (from several
  * host threads) race on the shared array.  Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_CUDA. */
 int nm_get_state_noalloc(nm_mesh mesh, double *m_out, double *t, double *dt);
@@ -218,6 +235,7 @@ int nm_h_eff_vjp(nm_mesh mesh, const void *m, const void *v, unsigned terms, dou
  * `checkpoint_every` steps from stored states (<= 0: 32).  weight, target: HOST FP64 nodal vector
  * fields (target may be NULL = 0).  Outputs (HOST FP64, each may be NULL except loss): loss; grad_Ms
  * (cell scalar field, dL/dMs); grad_m0 (nodal vector field, dL/dm(t0)); n_steps (accepted steps);
+ * with grad_Ms, grad_m0 and grad_h all NULL only the forward run and its loss are computed;
  * grad_h (3 values: dL/dh of the uniform applied field amplitude of nm_set_field, the design variable of
  * the paper's field-angle inverse problem, section "Inverse Problems").
  * The resident state ends at t_end.  Synchronises.  Errors: as nm_run_until, NM_ERR_OOM. */
@@ -244,6 +262,13 @@ int nm_adjoint_run(nm_mesh mesh, int method, double t_end, double rtol, double a
  * NM_ERR_STATE (no material or state), NM_ERR_OOM, NM_ERR_CUDA. */
 int nm_adjoint_continuous(nm_mesh mesh, double t_end, long n_steps, const double *weight, const double *target,
                           double *loss, double *grad_m0, double *grad_Ms, double *grad_h, double *m0_rec);
+
+/* Arithmetic ceiling of the current GPU for the roofline of ALU-bound kernels (the paper has no
+ * counterpart; it states the denominators of the FP64 path's roofline): a grid of independent fused
+ * multiply-add chains filling every SM, `reps` launches timed with CUDA events.  kind 0: FP32, 1: FP64.
+ * *flops_per_s receives 2 x the multiply-adds per second.  Synchronises.  Errors: NM_ERR_ARG,
+ * NM_ERR_CUDA. */
+int nm_measure_peak(int kind, int reps, double *flops_per_s);
 
 /* Sizes of the mesh: nodes, cells, padded FFT lengths P1 P2 P3, and the device bytes the mesh holds. */
 int nm_mesh_info(nm_mesh mesh, long *n_nodes, long *n_cells, int P[3], long *device_bytes);

@@ -84,6 +84,8 @@ SIGNATURES = [
     ("nm_get_state", _i, [_vp, _vp, _i, _Pd, _Pd]),
     ("nm_get_state_noalloc", _i, [_vp, _Pd, _Pd, _Pd]),
     ("nm_set_integrator", _i, [_vp, _i, _d, _i]),
+    ("nm_set_error_norm", _i, [_vp, _i]),
+    ("nm_measure_peak", _i, [_i, _i, _Pd]),
     ("nm_h_eff", _i, [_vp, _vp, _vp, _u, _d]),
     ("nm_set_terms", _i, [_vp, _u]),
     ("nm_set_dmi", _i, [_vp, _Pd, _d]),
@@ -143,6 +145,13 @@ def _host_f64(a, shape):
     if a.shape != tuple(shape):
         raise ValueError(f"expected shape {tuple(shape)}, got {a.shape}")
     return a
+
+
+def measure_peak(kind, reps=5) -> float:
+    """FLOP/s of fused multiply-add chains on the current GPU: kind 0 FP32, 1 FP64."""
+    out = np.zeros(1)
+    _check(load().nm_measure_peak(int(kind), int(reps), _pd(out)))
+    return float(out[0])
 
 
 def footprint_bytes(n, precision=F32) -> int:
@@ -243,6 +252,10 @@ class Mesh:
 
     def set_integrator(self, renormalise=True, dt_min=1e-22, max_rejections=50):
         _check(self.lib.nm_set_integrator(self._h, int(bool(renormalise)), float(dt_min), int(max_rejections)))
+
+    def set_error_norm(self, fp64_terms):
+        """FP32 meshes: form the per-node terms of the Dormand-Prince error norm in FP64 (True) or FP32."""
+        _check(self.lib.nm_set_error_norm(self._h, int(bool(fp64_terms))))
 
     # ---------------------------------------------------------------------------------- state
     def set_state(self, m, t=0.0, dt=1e-14):
@@ -364,16 +377,17 @@ class Mesh:
         return gm, gMs
 
     def adjoint_run(self, t_end, weight, target=None, method=DP54, rtol=1e-5, atol=1e-5, dt0=0.0,
-                    sample_dt=0.0, include_initial=False, checkpoint_every=32, field_grad=False):
+                    sample_dt=0.0, include_initial=False, checkpoint_every=32, field_grad=False, loss_only=False):
         """Forward integration to t_end with the sampled quadratic loss and its discrete adjoint.
         Returns (loss, dL/dMs (N1,N2,N3), dL/dm0 nodal, accepted steps), and dL/dh of the uniform applied
-        field (3,) as a fifth element when field_grad is set."""
+        field (3,) as a fifth element when field_grad is set.  loss_only: the forward run alone; the
+        gradients come back as None."""
         W = _host_f64(weight, self.nodes + (3,))
         tg = None if target is None else _host_f64(target, self.nodes + (3,))
         loss = ctypes.c_double()
-        gMs = np.zeros(self.n)
-        gm0 = np.zeros(self.nodes + (3,))
-        gh = np.zeros(3) if field_grad else None
+        gMs = None if loss_only else np.zeros(self.n)
+        gm0 = None if loss_only else np.zeros(self.nodes + (3,))
+        gh = np.zeros(3) if (field_grad and not loss_only) else None
         ns = ctypes.c_long()
         _check(self.lib.nm_adjoint_run(self._h, int(method), float(t_end), float(rtol), float(atol), float(dt0),
                                        float(sample_dt), _pd(W), _pd(tg), int(bool(include_initial)),

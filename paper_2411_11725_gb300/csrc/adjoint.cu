@@ -104,6 +104,7 @@ int heff_vjp_t(nm_mesh M, const void *m, const void *v, unsigned terms, double t
 extern "C" int nm_h_eff_vjp(nm_mesh M, const void *m, const void *v, unsigned terms, double t, void *grad_m,
                             void *grad_Ms)
 {
+    clear_error();
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     if (!m || !v || !grad_m) return fail(NM_ERR_ARG, "m, v and grad_m are required");
     if (terms & ~NM_TERMS_MASK) return fail(NM_ERR_ARG, "unknown term bits 0x%x", terms);
@@ -493,6 +494,17 @@ int adjoint_run_t(nm_mesh M, int method, double t_end, double rtol, double atol,
         }
     }
     const long n = (long)ts.size();
+    if (!grad_Ms && !grad_m0 && !grad_h) {
+        // the loss alone: no reverse sweep; the resident state stays at the end of the run
+        ADJ_TRY(set_ctl(M, t, dt));
+        M->k1_valid = false;
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+        release_all();
+        CUDA_TRY(cudaStreamSynchronize(M->st));
+        *loss_out = loss;
+        if (n_steps_out) *n_steps_out = n;
+        return NM_OK;
+    }
     double *m_end = nullptr;
     ADJ_TRY(galloc((void **)&m_end, nd3));
     CUDA_TRY(cudaMemcpyAsync(m_end, M->m, nd3, cudaMemcpyDeviceToDevice, M->st));
@@ -589,6 +601,7 @@ extern "C" int nm_adjoint_run(nm_mesh M, int method, double t_end, double rtol, 
                               long checkpoint_every, double *loss, double *grad_Ms, double *grad_m0, long *n_steps,
                               double *grad_h)
 {
+    clear_error();
     int rc = check_step_args(M, method, rtol, atol);
     if (rc) return rc;
     if (!weight || !loss) return fail(NM_ERR_ARG, "weight and loss are required");
@@ -797,6 +810,7 @@ extern "C" int nm_adjoint_continuous(nm_mesh M, double t_end, long n_steps, cons
                                      const double *target, double *loss, double *grad_m0, double *grad_Ms,
                                      double *grad_h, double *m0_rec)
 {
+    clear_error();
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
     if (!M->material_set) return fail(NM_ERR_STATE, "material not set");
     if (!M->state_set) return fail(NM_ERR_STATE, "no resident state");

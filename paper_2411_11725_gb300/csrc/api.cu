@@ -12,6 +12,8 @@
 
 static thread_local std::string g_last_error;
 
+void clear_error() { g_last_error.clear(); }
+
 int fail(int code, const char *fmt, ...)
 {
     char buf[512];
@@ -145,7 +147,7 @@ static void release(nm_mesh M)
     void *ptrs[] = {M->m, M->mf, M->y[0], M->y[1], M->hin, M->hout, M->inv_mass, M->vol, M->MsH, M->S, M->Nk, M->tw,
                     M->tw64, M->A_d, M->Ku_d, M->Ms_d, M->Ms64_d, M->Msh_d, M->hcell64_d, M->D_d, M->hdmi, M->ctl,
                     M->partials,
-                    M->mean_d, M->n_active_d, M->vj_w, M->vj_h, M->vj_q, M->vj_g, M->vj_H, M->vj_HW, M->vj_M,
+                    M->mean_d, M->n_active_d, M->n_bad_d, M->vj_w, M->vj_h, M->vj_q, M->vj_g, M->vj_H, M->vj_HW, M->vj_M,
                     M->vj_gMs};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -251,6 +253,7 @@ int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int 
     ALLOC(M->partials, 4 * 1024 * sizeof(double));
     ALLOC(M->mean_d, 4 * sizeof(double));
     ALLOC(M->n_active_d, sizeof(unsigned long long));
+    ALLOC(M->n_bad_d, sizeof(unsigned long long));
 #undef ALLOC
     if (cudaMallocHost(&M->hctl, sizeof(StepCtl)) != cudaSuccess ||
         cudaMallocHost(&M->mean_h, 4 * sizeof(double)) != cudaSuccess) {
@@ -534,6 +537,15 @@ extern "C" int nm_set_terms(nm_mesh M, unsigned terms)
     return NM_OK;
 }
 
+extern "C" int nm_set_error_norm(nm_mesh M, int fp64_terms)
+{
+    g_last_error.clear();
+    if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
+    M->err_f64_terms = fp64_terms ? 1 : 0;
+    free_graphs(M);
+    return NM_OK;
+}
+
 extern "C" int nm_set_integrator(nm_mesh M, int renormalise, double dt_min, int max_rejections)
 {
     if (!M) return fail(NM_ERR_ARG, "mesh is NULL");
@@ -566,11 +578,21 @@ extern "C" int nm_set_state(nm_mesh M, const double *m, int where, double t, dou
             src = tmp;
         }
     }
-    launch_aos_to_soa<double, double>(g, src, M->m, M->st);
+    CUDA_TRY(cudaMemsetAsync(M->n_bad_d, 0, sizeof(unsigned long long), M->st));
+    launch_aos_to_soa<double, double>(g, src, M->m, M->st, M->n_bad_d);
     CHECK_LAUNCH();
     if (tmp) CUDA_TRY(cudaFreeAsync(tmp, M->st));
+    unsigned long long n_bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&n_bad, M->n_bad_d, sizeof n_bad, cudaMemcpyDeviceToHost, M->st));
     StepCtl *h = M->hctl;
     CUDA_TRY(cudaStreamSynchronize(M->st));
+    M->k1_valid = false;
+    M->mf_valid = false;
+    if (n_bad) {
+        // the resident m now holds the rejected values: no integration until a valid state is set
+        M->state_set = false;
+        return fail(NM_ERR_NONFINITE, "m holds non-finite values at %llu nodes; state not set", n_bad);
+    }
     memset(h, 0, sizeof(StepCtl));
     h->t = t;
     h->dt = dt;
@@ -735,7 +757,7 @@ static void enqueue_dp5_step(nm_mesh M)
     }
     kb.n = ke.n = 6;
     launch_dp5_control<T>(g, M->m, kb, ke, (const T *)M->inv_mass, M->ctl, M->partials, M->n_active, M->max_rej,
-                          M->st, M->mf);
+                          M->st, M->mf, M->err_f64_terms != 0);
     marker(M)("dp5_error_control");
     KList ku = kb;
     ku.n = 5;  // b7 = 0

@@ -92,9 +92,9 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
 }
 
 // Per-block partial sums of ((dt sum_i e_i k_i) / (atol + rtol max(|m|, |m5|)))^2 over magnetic
-// nodes, m5 = m + dt sum_i b_i k_i.  The per-node terms follow the working precision of the slopes;
-// the sums are FP64.
-template <typename T>
+// nodes, m5 = m + dt sum_i b_i k_i.  The per-node terms follow the working precision of the slopes
+// (F64T: in FP64 for FP32 slopes too, from the FP64 m and FP64 coefficients); the sums are FP64.
+template <typename T, bool F64T = false>
 __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, const double *__restrict__ m,
                                                           KList kb, KList ke, const T *__restrict__ inv_mass,
                                                           const StepCtl *ctl, double *partials,
@@ -111,13 +111,35 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, 
         T part = 0;
         for (int c = 0; c < 3; ++c) {
             long i = c * ns + n;
-            T sb = 0, se = 0;
+            if (F64T && sizeof(T) == 4) {
+                // every operation of the term in FP64 (the FP32 slopes are exact in FP64)
+                double db = 0.0, de = 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j >= kb.n) break;
+                    const double kv = (double)((const T *)kb.p[j])[i];
+                    db += kb.a[j] * kv;
+                    de += ke.a[j] * kv;
+                }
+                const double m0 = m[i], m5 = m0 + dt * db;
+                const double sc = atol + rtol * fmax(fabs(m0), fabs(m5));
+                const double q = dt * de / sc;
+                acc += magnetic ? q * q : 0.0;
+                continue;
+            }
+            T sb = 0, se = 0, k1v = 0;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (j >= kb.n) break;
                 const T kv = ((const T *)kb.p[j])[i];
                 sb += kcoef<T>(kb, j) * kv;
-                se += kcoef<T>(ke, j) * kv;
+                if (sizeof(T) == 8) {
+                    se += kcoef<T>(ke, j) * kv;
+                } else if (j == 0) {
+                    k1v = kv;
+                } else {
+                    se += kcoef<T>(ke, j) * (kv - k1v);  // difference form (see dp5_err_term)
+                }
             }
             if (sizeof(T) == 8) {
                 const double m0 = m[i], m5 = m0 + dt * (double)sb;
@@ -143,6 +165,12 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err(long n_nodes, long ns, 
 // load (16-byte vectors; every component array starts on a 256-byte boundary), fewer and longer
 // requests for the 25 streams the norm reads.  Nodes past the last full group of four go through the
 // scalar terms of block 0.
+//
+// The error combination sum_j e_j k_j (e_j = b_j - b*_j, first slope k_1) is formed in FP32 as
+// sum_{j>1} e_j (k_j - k_1).  The weights sum to zero, so this is the same quantity; the slopes of one
+// step are close to each other, so their differences are exact in FP32 and the combination keeps its
+// relative accuracy when it is far smaller than the slopes (small steps), where the direct sum with
+// FP32-rounded weights would leave a residue of about 1e-8 |k_1|.
 __device__ __forceinline__ float dp5_err_term(float m0, float sb, float se, float dtf, float rtol, float atol)
 {
     const float m5 = m0 + dtf * sb;
@@ -165,14 +193,19 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err_f4(long n_nodes, long n
         float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float4 sb = make_float4(0.f, 0.f, 0.f, 0.f), se = sb;
+            float4 sb = make_float4(0.f, 0.f, 0.f, 0.f), se = sb, k1 = sb;
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (j >= kb.n) break;
                 const float4 kv = reinterpret_cast<const float4 *>((const float *)kb.p[j] + c * ns)[q];
                 const float b = kb.af[j], e = ke.af[j];
                 sb.x += b * kv.x; sb.y += b * kv.y; sb.z += b * kv.z; sb.w += b * kv.w;
-                se.x += e * kv.x; se.y += e * kv.y; se.z += e * kv.z; se.w += e * kv.w;
+                if (j == 0) {
+                    k1 = kv;
+                } else {
+                    se.x += e * (kv.x - k1.x); se.y += e * (kv.y - k1.y);
+                    se.z += e * (kv.z - k1.z); se.w += e * (kv.w - k1.w);
+                }
             }
             const float4 m0 = reinterpret_cast<const float4 *>(mf + c * ns)[q];
             part.x += dp5_err_term(m0.x, sb.x, se.x, dtf, rtol, atol);
@@ -189,12 +222,13 @@ __global__ void __launch_bounds__(kRedThreads) k_dp5_err_f4(long n_nodes, long n
         float part = 0.f;
         for (int c = 0; c < 3; ++c) {
             const long i = c * ns + n;
-            float sb = 0.f, se = 0.f;
+            float sb = 0.f, se = 0.f, k1 = 0.f;
             for (int j = 0; j < 8; ++j) {
                 if (j >= kb.n) break;
                 const float kv = ((const float *)kb.p[j])[i];
                 sb += kb.af[j] * kv;
-                se += ke.af[j] * kv;
+                if (j == 0) k1 = kv;
+                else se += ke.af[j] * (kv - k1);
             }
             part += dp5_err_term(mf[i], sb, se, dtf, rtol, atol);
         }
@@ -494,7 +528,8 @@ __global__ void __launch_bounds__(1024) k_mean_final(const double *partials, int
 // host-device link).  Block (32, 8); grid (tiles along n3, tiles along n1, nn2).
 constexpr int kTT = 32;
 template <typename Tin, typename Tout>
-__global__ void __launch_bounds__(256) k_aos_to_soa(Geom g, const Tin *__restrict__ a, Tout *__restrict__ s)
+__global__ void __launch_bounds__(256) k_aos_to_soa(Geom g, const Tin *__restrict__ a, Tout *__restrict__ s,
+                                                    unsigned long long *__restrict__ nonfinite)
 {
     __shared__ Tout tile[3][kTT][kTT + 1];
     const int n2 = blockIdx.z;
@@ -504,9 +539,11 @@ __global__ void __launch_bounds__(256) k_aos_to_soa(Geom g, const Tin *__restric
         const int n1 = n1_0 + r, n3 = n3_0 + tx;
         if (n1 < g.nn1 && n3 < g.nn3) {
             const long b = (((long)n1 * g.nn2 + n2) * g.nn3 + n3) * 3;
-            tile[0][r][tx] = (Tout)a[b];
-            tile[1][r][tx] = (Tout)a[b + 1];
-            tile[2][r][tx] = (Tout)a[b + 2];
+            const Tin v0 = a[b], v1 = a[b + 1], v2 = a[b + 2];
+            if (nonfinite && !(isfinite(v0) && isfinite(v1) && isfinite(v2))) atomicAdd(nonfinite, 1ull);
+            tile[0][r][tx] = (Tout)v0;
+            tile[1][r][tx] = (Tout)v1;
+            tile[2][r][tx] = (Tout)v2;
         }
     }
     __syncthreads();
@@ -641,12 +678,18 @@ int reduction_blocks(long n_nodes)
 template <typename T>
 void launch_dp5_control(const Geom &g, const double *m, const KList &kb, const KList &ke, const T *inv_mass,
                         StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st,
-                        const float *mf)
+                        const float *mf, bool f64_terms)
 {
     // up to 4096 partial sums (the mesh's partials buffer), so that enough loads are in flight
     long nbl = (g.n_nodes + kRedThreads - 1) / kRedThreads;
     const int nb = (int)(nbl > 4096 ? 4096 : (nbl < 1 ? 1 : nbl));
     if constexpr (sizeof(T) == 4) {
+        if (f64_terms) {
+            k_dp5_err<T, true><<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, m, fk(kb), fk(ke), inv_mass, ctl,
+                                                           partials, nullptr);
+            k_dp5_ctl<<<1, 1024, 0, st>>>(partials, nb, n_active, ctl, max_rej);
+            return;
+        }
         if (mf) {
             k_dp5_err_f4<<<nb, kRedThreads, 0, st>>>(g.n_nodes, g.ns, fk(kb), fk(ke), (const float *)inv_mass, ctl,
                                                      partials, mf);
@@ -690,10 +733,10 @@ void launch_mean(const Geom &g, const double *m, const T *vol, double *partials,
 }
 
 template <typename Tin, typename Tout>
-void launch_aos_to_soa(const Geom &g, const Tin *a, Tout *s, cudaStream_t st)
+void launch_aos_to_soa(const Geom &g, const Tin *a, Tout *s, cudaStream_t st, unsigned long long *nonfinite)
 {
     const dim3 grid(div_up(g.nn3, kTT), div_up(g.nn1, kTT), g.nn2);
-    k_aos_to_soa<Tin, Tout><<<grid, dim3(kTT, 8), 0, st>>>(g, a, s);
+    k_aos_to_soa<Tin, Tout><<<grid, dim3(kTT, 8), 0, st>>>(g, a, s, nonfinite);
 }
 
 template <typename Tin, typename Tout>
@@ -726,7 +769,7 @@ void launch_node_volume(const Geom &g, const double *Ms, double Ms0, double V, T
     template void launch_stage_input<T>(const Geom &, const double *, const KList &, const StepCtl *, T *,       \
                                         cudaStream_t, const float *);                                                         \
     template void launch_dp5_control<T>(const Geom &, const double *, const KList &, const KList &, const T *,   \
-                                        StepCtl *, double *, double, int, cudaStream_t, const float *);                       \
+                                        StepCtl *, double *, double, int, cudaStream_t, const float *, bool);                 \
     template void launch_dp5_update<T>(const Geom &, double *, const KList &, const T *, T *, const StepCtl *,  \
                                        int, cudaStream_t, float *);                                                     \
     template void launch_rk4_update<T>(const Geom &, double *, const KList &, StepCtl *, int, cudaStream_t, float *);    \
@@ -737,9 +780,12 @@ void launch_node_volume(const Geom &g, const double *Ms, double Ms0, double V, T
 
 NM_INST(float)
 NM_INST(double)
-template void launch_aos_to_soa<float, float>(const Geom &, const float *, float *, cudaStream_t);
-template void launch_aos_to_soa<double, float>(const Geom &, const double *, float *, cudaStream_t);
-template void launch_aos_to_soa<double, double>(const Geom &, const double *, double *, cudaStream_t);
+template void launch_aos_to_soa<float, float>(const Geom &, const float *, float *, cudaStream_t,
+                                              unsigned long long *);
+template void launch_aos_to_soa<double, float>(const Geom &, const double *, float *, cudaStream_t,
+                                               unsigned long long *);
+template void launch_aos_to_soa<double, double>(const Geom &, const double *, double *, cudaStream_t,
+                                                unsigned long long *);
 template void launch_soa_to_aos<float, float>(const Geom &, const float *, float *, cudaStream_t);
 template void launch_soa_to_aos<float, double>(const Geom &, const float *, double *, cudaStream_t);
 template void launch_soa_to_aos<double, double>(const Geom &, const double *, double *, cudaStream_t);

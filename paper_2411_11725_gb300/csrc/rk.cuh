@@ -29,9 +29,10 @@ template <typename T>
 void launch_stage_input(const Geom &g, const double *m, const KList &k, const StepCtl *ctl, T *y, cudaStream_t st,
                         const float *mf = nullptr);
 template <typename T>
+// f64_terms (FP32 slopes): every per-node term of the error norm in FP64 instead of FP32
 void launch_dp5_control(const Geom &g, const double *m, const KList &kb, const KList &ke, const T *inv_mass,
                         StepCtl *ctl, double *partials, double n_active, int max_rej, cudaStream_t st,
-                        const float *mf = nullptr);
+                        const float *mf = nullptr, bool f64_terms = false);
 template <typename T>
 void launch_dp5_update(const Geom &g, double *m, const KList &kb, const T *k7, T *k1, const StepCtl *ctl, int renorm,
                        cudaStream_t st, float *mf = nullptr);
@@ -41,7 +42,9 @@ void launch_rk4_update(const Geom &g, double *m, const KList &kb, StepCtl *ctl, 
 template <typename T>
 void launch_mean(const Geom &g, const double *m, const T *vol, double *partials, double *out, cudaStream_t st);
 template <typename Tin, typename Tout>
-void launch_aos_to_soa(const Geom &g, const Tin *a, Tout *s, cudaStream_t st);
+// node-major (n1, n2, n3, 3) -> SoA planes; with `nonfinite` set, also counts the nodes holding a
+// non-finite component into *nonfinite (device)
+void launch_aos_to_soa(const Geom &g, const Tin *a, Tout *s, cudaStream_t st, unsigned long long *nonfinite = nullptr);
 template <typename Tin, typename Tout>
 void launch_soa_to_aos(const Geom &g, const Tin *s, Tout *a, cudaStream_t st);
 template <typename Tout>

@@ -160,3 +160,25 @@ def test_uniform_m_mean_demag_is_prism_factor(nmgb, precision, n):
     ref = -p.Ms * aharoni_factors(np.array(n) * np.array(p.dx)) * mu
     tol = {0: 1e-5, 1: 1e-11}[precision]
     assert np.abs(mean - ref).max() <= tol * p.Ms
+
+
+@pytest.mark.parametrize("terms_name", ["DEMAG", "ALL"])
+def test_fp32_dense_random_state_matches_fp64_path(nmgb, terms_name):
+    """The state the benchmark integrates (dense random unit m on 1024x1024x32 cells): the FP32 field,
+    demag alone and all terms, against the FP64 path on the same FP32-rounded input (the FP64 path
+    matches the oracle at 1e-12 on the sampled outputs above and on every small mesh).  Bar: rel-L2 <=
+    1e-5, as for the small meshes."""
+    import torch
+    p = _problem(N)
+    terms = getattr(nmgb, terms_name)
+    m = torch.tensor(rounded(p.m0, 0), dtype=torch.float64, device="cuda")
+    out = {}
+    for precision in (1, 0):
+        me = gpu_mesh(nmgb, p, precision)
+        h = me.h_eff(m.to(me.dtype), terms, 0.0)
+        out[precision] = h.double()
+        del h
+        me.close()
+        torch.cuda.empty_cache()
+    err = (torch.linalg.vector_norm(out[0] - out[1]) / torch.linalg.vector_norm(out[1])).item()
+    assert err <= 1e-5, err
