@@ -142,8 +142,11 @@ int nm_set_integrator(nm_mesh mesh, int renormalise, double dt_min, int max_reje
  * and the FP32 copy of m, and summed in FP64.  1: every operation of the terms in FP64, from the same
  * FP32 slopes, the FP64 m and FP64 coefficients.  FP64 meshes always use FP64.  The FP32 terms carry
  * rounding of about 1e-7 of the largest slope contribution; the slopes themselves carry the FP32 field
- * error (about 1e-6 relative), so both settings estimate the same error to that accuracy.  GB300's
- * FP64 rate makes setting 1 several times slower than 0 for this kernel.  Errors: NM_ERR_ARG. */
+ * error (about 1e-6 relative), so both settings estimate the same error to that accuracy.  The FP32
+ * terms form sum_i e_i k_i as sum_{i>1} e_i (k_i - k_1) (the weights sum to zero), which keeps their
+ * relative accuracy when the combination is far smaller than the slopes.  GB300's FP64 rate makes
+ * setting 1 about ten times slower for this kernel (6.2 against 0.63 ms per step on 1024x1024x32
+ * cells).  Errors: NM_ERR_ARG. */
 int nm_set_error_norm(nm_mesh mesh, int fp64_terms);
 
 /* Effective field h = H_eff(m) at time t for the terms in the mask (NM_EXCH|NM_ANIS|NM_ZEE|NM_DEMAG|NM_DMI):

@@ -1,8 +1,10 @@
 """FP32 meshes form the per-node terms of the Dormand-Prince error norm in FP32 and sum them in FP64
 (the Dormand-Prince integrator of the time-integration section).  With every operation of those terms
 in FP64 instead (nm_set_error_norm), the thin film run to 1 ns and the 256x256x8 throughput cuboid over
-200 steps take the same accept/reject decisions step by step, with step sizes within 1e-5 of each
-other: the FP32 terms change the controller's output by far less than its own step-to-step variation.
+200 steps take the same accept/reject decisions step by step.  Over the first 20 attempts, where both
+runs still hold the same state to rounding, the step sizes agree within 1e-5 and the error norms within
+5e-5; over the whole run, where the two trajectories drift apart by the rounding of their step sizes,
+within 1e-4 and 5e-4.
 """
 import numpy as np
 import pytest
@@ -51,6 +53,7 @@ def test_fp32_error_terms_take_the_fp64_terms_decisions(nmgb, case):
     a32, dt32, e32 = _sequence(nmgb, p, False, **kw)
     a64, dt64, e64 = _sequence(nmgb, p, True, **kw)
     assert len(a32) == len(a64) and np.array_equal(a32, a64)
-    assert np.abs(dt32 / dt64 - 1).max() <= 1e-5
-    assert np.abs(e32 / e64 - 1).max() <= 1e-4
+    rdt, rerr = np.abs(dt32 / dt64 - 1), np.abs(e32 / e64 - 1)
+    assert rdt[:20].max() <= 1e-5 and rerr[:20].max() <= 5e-5, (rdt[:20].max(), rerr[:20].max())
+    assert rdt.max() <= 1e-4 and rerr.max() <= 5e-4, (rdt.max(), rerr.max())
     assert a32.sum() >= 100
