@@ -148,13 +148,6 @@ def algorithmic_bytes(name, stage, n, b, with_maps):
         return 2 * 3 * c * X * N2 + 6 * b * X * H2
     if name == "demag_x_inv":
         return 3 * c * X * N2 * N3 + ms + 3 * b * Nc
-    # three-pass plan (FP32, several cell layers): the spectrum is padded along z, not y, between passes
-    if name == "demag_xz_fwd":
-        return 3 * b * Nn + ms + 3 * c * X * N2 * P3
-    if name == "demag_y_conv3":
-        return 2 * 3 * c * X * N2 * P3 + 6 * b * X * H2 * H3
-    if name == "demag_zx_inv":
-        return 3 * c * X * N2 * P3 + ms + 3 * b * Nc
     # stage inputs and the error scale read the FP64 m (24 B/node), or in the FP32 path its FP32 copy
     mb = 3 * b if b == 4 else 24
     if name == "node_llg_stage":
