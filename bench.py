@@ -168,6 +168,40 @@ def algorithmic_bytes(name, stage, n, b, with_maps):
     return 0
 
 
+def fp64_line(nmgb, value64, ms64, k64, value32, prof64, nn, wl_key):
+    """The plain FP64 path: node-steps/s, and its roofline against GB300's FP64 rate (ALU-bound: the FP64
+    pipe is far slower than HBM here).  peak = the library's FP64 fused multiply-add probe; FP64
+    operations per node and step from the committed ncu counts (profiles/fp64_flops.txt: DADD + DMUL +
+    2 DFMA of one step, per node), used only while the sources match the capture."""
+    out = {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64 if k64 else None, "steps": k64,
+           "fp32_over_fp64": value32 / value64 if value64 else None}
+    if not value64:
+        return out
+    if prof64:
+        out["kernels_ms"] = {}
+        for name, t in prof64:
+            out["kernels_ms"][name] = out["kernels_ms"].get(name, 0.0) + t
+    try:
+        peak = nmgb.measure_peak(1)
+    except Exception as e:
+        out["roofline"] = {"error": f"{type(e).__name__}: {e}"}
+        return out
+    flops_node = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "fp64_flops.txt")) as f:
+            d = json.load(f)
+        if d.get("csrc_sha") == csrc_hash():
+            flops_node = float(d["flops_per_node_step"])
+    except Exception:
+        pass
+    achieved = flops_node * nn * (value64 / nn) / 1e12 if flops_node else None
+    out["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": peak / 1e12,
+                       "peak_source": "nm_measure_peak(FP64): fused multiply-add chains on every SM",
+                       "flops_per_node_step": flops_node, "achieved": achieved,
+                       "frac": achieved / (peak / 1e12) if achieved else None}
+    return out
+
+
 def traffic_for(name, workload_key):
     """dram bytes per launch from the committed ncu summary, if it matches the current kernels."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
@@ -372,7 +406,7 @@ def run_ours(args, rank, world, dist):
     me.close()
     del me
     # ---- plain FP64 path on the same workload (fewer steps: it is several times slower)
-    value64, ms64, k64 = None, None, 0
+    value64, ms64, k64, prof64 = None, None, 0, None
     if args.fp64_steps > 0:
         k64 = max(2, min(K, args.fp64_steps))
         me = make(nmgb.F64)
@@ -381,6 +415,11 @@ def run_ours(args, rank, world, dist):
         ms64, acc64, _ = timed_steps(me, k64)
         ms64 = max_over_ranks(ms64)
         value64 = nn * sum_over_ranks(acc64) / (ms64 * 1e-3)
+        # one step launch by launch inside an NVTX range (the ncu capture of its FP64 operations selects it)
+        torch.cuda.nvtx.range_push("fp64_profile_step")
+        prof64 = me.profile_step(nmgb.DP54, reps=1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         me.close()
         del me
 
@@ -426,6 +465,12 @@ def run_ours(args, rank, world, dist):
             wire = run_wire(nmgb, args.film_steps)
         except Exception as e:
             wire = {"error": f"{type(e).__name__}: {e}"}
+    workloads = None
+    if args.workloads and rank == 0:
+        try:
+            workloads = run_workloads(nmgb)
+        except Exception as e:  # a side measurement: report it, keep the headline line
+            workloads = {"error": f"{type(e).__name__}: {e}"}
     cufft = None
     if args.cufft_reps > 0 and rank == 0:
         dem = [k for k in groups if k.startswith("demag_")]
@@ -459,8 +504,7 @@ def run_ours(args, rank, world, dist):
                   "evals": evals_tot,
                   "note": "the paper's timing metric: integration time / number of field evaluations (six per "
                           "DP5(4) step with FSAL, accepted or rejected), here per node"},
-        "fp64": {"value": value64, "unit": UNIT, "ms_per_step": ms64 / k64 if k64 else None, "steps": k64,
-                 "fp32_over_fp64": value / value64 if value64 else None},
+        "fp64": fp64_line(nmgb, value64, ms64, k64, value, prof64, nn, wl_key),
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(24 * nn),
                 "d2h_bytes_per_step": 32 + 128, "steps": ke,
                 "note": "per step through the public API: nm_set_state from pinned host m (the step's input), "
@@ -477,6 +521,7 @@ def run_ours(args, rank, world, dist):
         "serving": serving,
         "gradients": gradients,
         "cufft_baseline": cufft,
+        "workloads": workloads,
         "thin_film_2d_basis": film,
         "wire_1d_basis": wire,
         "clocks": clocks,
@@ -652,6 +697,110 @@ def run_gradients(nmgb, n_steps, grid=(256, 256, 8), dt=1e-14):
     return out
 
 
+def run_workloads(nmgb, sweep_steps=10):
+    """Absolute node-steps/s of the other workloads (wall time, synchronised, FP32 field with FP64 state
+    and plain FP64): the 16x16x4 cuboid over its 1000 RK4 steps, the 200x50x1 film by Dormand-Prince to
+    1 ns (with the FP32-FP64 gap of the time-averaged mean m), the 256x256x8 and 512x512x16 throughput
+    cuboids over `sweep_steps` DP5 steps, and the 256x64x1 waveguide over 2 ns with its Ms gradient
+    (loss on the right 16 cells, RK4 steps of 0.25 ps, checkpoints every ceil(sqrt(n)) steps)."""
+    import math
+    out = {}
+
+    def timed(fn):
+        t0 = time.perf_counter()
+        r = fn()
+        return r, time.perf_counter() - t0
+
+    # cuboid 16x16x4, 1000 RK4 steps of 1e-14 s
+    p = inp.cuboid_rk4(0)
+    nn = int(np.prod(p.nodes))
+    res = {"workload": "cuboid 16x16x4 cells of 2 nm, exchange + demag + Zeeman, 1000 RK4 steps of 1e-14 s"}
+    for prec, name in ((nmgb.F32, "fp32"), (nmgb.F64, "fp64")):
+        me = nmgb.Mesh(p.n, p.dx, prec)
+        me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+        me.set_zeeman(p.h_uniform)
+        me.set_terms(p.terms)
+        me.set_state(p.m0, 0.0, 1e-14)
+        me.run_until(2e-13, nmgb.RK4, dt0=1e-14)  # warm-up (graphs)
+        me.set_state(p.m0, 0.0, 1e-14)
+        (_, na, _), el = timed(lambda: me.run_until(1e-11, nmgb.RK4, dt0=1e-14))
+        res[name] = {"node_steps_per_s": nn * na / el, "ms_per_step": el / na * 1e3, "steps": na}
+        me.close()
+    out["cuboid_16x16x4_rk4"] = res
+    # thin film 200x50x1 to 1 ns
+    p = inp.thin_film(0)
+    x = p.extra
+    nn = int(np.prod(p.nodes))
+    res = {"workload": "film 200x50x1 cells of 2.5x2.5x3 nm, exchange + demag + Zeeman, DP5(4) to 1 ns, "
+                       "rtol=atol=1e-5, 1 ps samples of the mean m"}
+    avg = {}
+    for prec, name in ((nmgb.F32, "fp32"), (nmgb.F64, "fp64")):
+        me = nmgb.Mesh(p.n, p.dx, prec)
+        me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+        me.set_zeeman(p.h_uniform)
+        me.set_terms(p.terms)
+        me.set_state(p.m0, 0.0, x["dt0"])
+        me.run_until(2e-12, nmgb.DP54, x["rtol"], x["atol"], dt0=x["dt0"])  # warm-up
+        me.set_state(p.m0, 0.0, x["dt0"])
+        (smp, na, nr), el = timed(lambda: me.run_until(x["t_end"], nmgb.DP54, x["rtol"], x["atol"], dt0=x["dt0"],
+                                                       sample_dt=x["sample_dt"]))
+        res[name] = {"node_steps_per_s": nn * na / el, "ms_per_step": el / (na + nr) * 1e3, "accepted": na,
+                     "rejected": nr}
+        avg[name] = (0.5 * (smp[0] + smp[-1]) + smp[1:-1].sum(axis=0)) / (len(smp) - 1)
+        me.close()
+    res["time_averaged_mean_m_gap_fp32_fp64"] = float(np.abs(avg["fp32"] - avg["fp64"]).max())
+    out["thin_film_200x50x1_dp5_1ns"] = res
+    # throughput sweep points
+    for grid in ((256, 256, 8), (512, 512, 16)):
+        p = inp.throughput(grid, seed=3, with_m0=False)
+        m0 = inp.unit_vectors(np.random.default_rng(3), p.nodes)
+        nn = int(np.prod(p.nodes))
+        res = {"workload": f"cuboid {grid[0]}x{grid[1]}x{grid[2]} cells of 3 nm, throughput material, DP5(4) "
+                           f"rtol=atol=1e-5, {sweep_steps} steps"}
+        for prec, name in ((nmgb.F32, "fp32"), (nmgb.F64, "fp64")):
+            me = nmgb.Mesh(p.n, p.dx, prec)
+            me.set_material(p.Ms, p.A, p.Ku, p.axis, p.alpha, p.gamma)
+            me.set_terms(p.terms)
+            me.set_state(m0, 0.0, 1e-15)
+            me.run_steps(3, nmgb.DP54, 1e-5, 1e-5)
+            me.sync()
+            a0, r0, _ = me.counters()
+            _, el = timed(lambda: (me.run_steps(sweep_steps, nmgb.DP54, 1e-5, 1e-5), me.sync()))
+            a1, r1, _ = me.counters()
+            res[name] = {"node_steps_per_s": nn * (a1 - a0) / el, "ms_per_step": el / ((a1 - a0) + (r1 - r0)) * 1e3}
+            me.close()
+        res["fp32_over_fp64"] = res["fp32"]["node_steps_per_s"] / res["fp64"]["node_steps_per_s"]
+        out[f"cuboid_{grid[0]}x{grid[1]}x{grid[2]}"] = res
+    # waveguide inverse problem over 2 ns
+    p = inp.waveguide(0)
+    T, sdt, dt = p.extra["t_end"], p.extra["sample_dt"], 2.5e-13
+    n_steps = int(round(T / dt))
+    C = math.ceil(math.sqrt(n_steps))
+    nn = int(np.prod(p.nodes))
+    W = np.zeros(p.nodes + (3,))
+    W[p.n[0] - 16:, :, :, 1] = 1.0
+    W /= W[..., 1].sum() * int(round(T / sdt))
+    res = {"workload": f"waveguide 256x64x1 cells of 4x4x10 nm, Ms map, 2 GHz drive, loss = mean m_y^2 over the "
+                       f"right 16 cells and 1 ps samples in [0, 2 ns], {n_steps} RK4 steps of 0.25 ps, "
+                       f"checkpoints every {C} steps, FP32 field"}
+    me = nmgb.Mesh(p.n, p.dx, nmgb.F32)
+    me.set_material(p.Ms_cells(), p.A, 0.0, p.axis, p.alpha, p.gamma)
+    me.set_zeeman((0, 0, 0), h_cell=p.h_cell, cell_freq=p.cell_freq, cell_phase=p.cell_phase)
+    me.set_terms(p.terms)
+    me.set_state(p.m0, 0.0, dt)
+    me.adjoint_run(2e-11, W, None, nmgb.RK4, dt0=dt, sample_dt=sdt, checkpoint_every=C)  # warm-up
+    me.set_state(p.m0, 0.0, dt)
+    (fwd, el_f) = timed(lambda: me.adjoint_run(T, W, None, nmgb.RK4, dt0=dt, sample_dt=sdt, checkpoint_every=C,
+                                               loss_only=True))
+    me.set_state(p.m0, 0.0, dt)
+    (grad, el_g) = timed(lambda: me.adjoint_run(T, W, None, nmgb.RK4, dt0=dt, sample_dt=sdt, checkpoint_every=C))
+    me.close()
+    res.update({"forward_s": el_f, "forward_node_steps_per_s": nn * fwd[3] / el_f, "gradient_s": el_g,
+                "gradient_over_forward": el_g / el_f, "steps": fwd[3], "loss": fwd[0]})
+    out["waveguide_256x64x1_gradient_2ns"] = res
+    return out
+
+
 def serving_kwargs(i, p):
     return dict(n=p.n, dx=p.dx, m0=inp.serving_m0(p), t_end=p.extra["t_end"], Ms=p.Ms, A=p.A, Ku=p.Ku,
                 axis=p.axis, alpha=p.alpha, gamma=p.gamma, h=p.h_uniform, terms=p.terms, rtol=p.extra["rtol"],
@@ -727,6 +876,7 @@ def main():
     ap.add_argument("--serve-max-active", type=int, default=16)
     ap.add_argument("--grad-steps", type=int, default=16, help="RK4 steps of the gradient timing leg (0: skip)")
     ap.add_argument("--film-steps", type=int, default=10, help="DP5 steps of the 2D-basis film and 1D-basis wire legs (0: skip)")
+    ap.add_argument("--workloads", type=int, default=1, help="absolute rates of the other workloads (0: skip)")
     ap.add_argument("--cufft-reps", type=int, default=3,
                     help="timed repetitions of the cuFFT zero-padded convolution baseline (0: skip)")
     args = ap.parse_args()
