@@ -118,7 +118,8 @@ class ClockSampler:
 
 
 def algorithmic_bytes(name, stage, n, b, with_maps):
-    """Bytes a launch must move at minimum ('Kernels and their rooflines').
+    """Bytes a launch must move at minimum: its inputs read once and its outputs written once, with the
+    zero padding of the FFT grid neither read nor written (the pruned passes skip it).
     n = (N1, N2, N3); b = bytes per real (4 or 8); stage = DP5 stage index of node kernels."""
     N1, N2, N3 = n
     Nn = (N1 + 1) * (N2 + 1) * (N3 + 1)
