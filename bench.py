@@ -872,7 +872,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--fp64-steps", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--serve-requests", type=int, default=40, help="requests per serving load level (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests per serving load level (0: skip)")
     ap.add_argument("--serve-budget-gb", type=float, default=2.0)
     ap.add_argument("--serve-max-active", type=int, default=16)
     ap.add_argument("--grad-steps", type=int, default=16, help="RK4 steps of the gradient timing leg (0: skip)")
