@@ -243,21 +243,35 @@ __global__ void __launch_bounds__(kXiThreads<T>, sizeof(T) == 4 ? 16 : 4)
         const Cx<T> Xc = conj(Xq);
         return (Xk + Xc) + mul_si((Xk - Xc) * conj(tw[k << wsh]), 1);
     };
-#pragma unroll 4
-    for (int t = threadIdx.x; t < nl * H; t += blockDim.x) {
-        const int l = t >> (LG - 1 < 0 ? 0 : LG - 1), k = t & (H - 1);
-        const Cx<T> *s = b.S + info[l].spec;
-        Cx<T> *z = buf + l * LSZ;
-        if (k == 0) {
-            z[0] = zk(s[0], s[Q], 0);
-            if (H > 0 && Q > 1) {
-                const Cx<T> Xh = s[H];
-                z[f3::pad16c(H)] = zk(Xh, Xh, H);
+    // the spectrum reads of KB pairs per thread are issued together, before any of them is used
+    constexpr int KB = 8;
+    for (int t0 = threadIdx.x; t0 < nl * H; t0 += KB * blockDim.x) {
+        Cx<T> xa[KB], xb[KB];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t >= nl * H) break;
+            const int l = t >> (LG - 1 < 0 ? 0 : LG - 1), k = t & (H - 1);
+            const Cx<T> *s = b.S + info[l].spec;
+            xa[u] = s[k];
+            xb[u] = s[k == 0 ? Q : Q - k];
+        }
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
+            const int t = t0 + u * blockDim.x;
+            if (t >= nl * H) break;
+            const int l = t >> (LG - 1 < 0 ? 0 : LG - 1), k = t & (H - 1);
+            Cx<T> *z = buf + l * LSZ;
+            if (k == 0) {
+                z[0] = zk(xa[u], xb[u], 0);
+                if (H > 0 && Q > 1) {
+                    const Cx<T> Xh = b.S[info[l].spec + H];
+                    z[f3::pad16c(H)] = zk(Xh, Xh, H);
+                }
+            } else {
+                z[f3::pad16c(k)] = zk(xa[u], xb[u], k);
+                z[f3::pad16c(Q - k)] = zk(xb[u], xa[u], Q - k);
             }
-        } else {
-            const Cx<T> Xk = s[k], Xq = s[Q - k];
-            z[f3::pad16c(k)] = zk(Xk, Xq, k);
-            z[f3::pad16c(Q - k)] = zk(Xq, Xk, Q - k);
         }
     }
     __syncthreads();
@@ -525,8 +539,48 @@ __global__ void __launch_bounds__(ZRTile<LG, kZRSplit<LG>>::THREADS, kZRSplit<LG
         const T *ten = reinterpret_cast<const T *>(buf + nl * P3);
         constexpr int tstride = H3 * KY * G, npts = KY * G * P3;
         const int h2 = g.P2 >> 1;
+        if constexpr (!Z::TSM) {
+            // the tensor comes from L2: all of a thread's tensor reads are issued before the products
+            constexpr int NPT = (npts + Z::THREADS - 1) / Z::THREADS;
+            Ten6<T> tv[NPT];
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) {
+                const int t = threadIdx.x + u * Z::THREADS;
+                const int gg = t % G, qr = t / G, rr = qr % KY, q = qr / KY;
+                const int a2 = a20 + rr;
+                if (t >= npts || a2 >= g.H2) continue;
+                const int kz = S * (q % D) + q / D;
+                const int a3 = kz <= H ? kz : P3 - kz;
+                const T *tp = b.Nk + ((long)a3 * g.H2 + a2) * g.Xp + kx0 + gg;
+                const long tc = g.t_comp;
+                tv[u].xx = __ldg(tp);
+                tv[u].yy = __ldg(tp + tc);
+                tv[u].zz = __ldg(tp + 2 * tc);
+                tv[u].xy = __ldg(tp + 3 * tc);
+                tv[u].xz = __ldg(tp + 4 * tc);
+                tv[u].yz = __ldg(tp + 5 * tc);
+            }
+#pragma unroll
+            for (int u = 0; u < NPT; ++u) {
+                const int t = threadIdx.x + u * Z::THREADS;
+                const int gg = t % G, qr = t / G, rr = qr % KY, q = qr / KY;
+                const int a2 = a20 + rr;
+                if (t >= npts || a2 >= g.H2) continue;
+                const int kz = S * (q % D) + q / D;
+                const T s3 = kz <= H ? T(1) : T(-1);
+                Ten6<T> tt = tv[u];
+                tt.xz *= s3;
+                tt.yz *= s3;
+                Cx<T> *p = buf + q * nl + rr * G + gg;
+                tensor_mul(tt, T(1), p, p + R2 * G, p + 2 * R2 * G);
+                if (a2 > 0 && a2 < h2) {
+                    Cx<T> *pm = p + KY * G;
+                    tensor_mul(tt, T(-1), pm, pm + R2 * G, pm + 2 * R2 * G);
+                }
+            }
+        }
 #pragma unroll 2
-        for (int t = threadIdx.x; t < npts; t += Z::THREADS) {
+        for (int t = threadIdx.x; Z::TSM && t < npts; t += Z::THREADS) {
             const int gg = t % G, qr = t / G, rr = qr % KY, q = qr / KY;
             const int a2 = a20 + rr;
             if (a2 >= g.H2) continue;
