@@ -298,8 +298,26 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const 
         const int k = j & (NS - 1);
         if (NS > 1) {
             const int kk = k << sh;
+            if constexpr (R == 16) {
+                // w^r for r < 16 from the four table values w, w^2, w^4, w^8 (four loads in flight together
+                // instead of fifteen; the other powers are at most three products away, a few roundings)
+                Cx<T> w[16];
+                w[1] = tw[kk];
+                w[2] = tw[2 * kk];
+                w[4] = tw[4 * kk];
+                w[8] = tw[8 * kk];
+                w[3] = w[1] * w[2];
+                w[5] = w[4] * w[1];
+                w[6] = w[4] * w[2];
+                w[7] = w[4] * w[3];
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[c][r] = twmul<T, DIR>(v[c][r], tw[kk * r]);
+                for (int r = 9; r < 16; ++r) w[r] = w[8] * w[r - 8];
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[c][r] = twmul<T, DIR>(v[c][r], w[r]);
+            } else {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[c][r] = twmul<T, DIR>(v[c][r], tw[kk * r]);
+            }
         }
         dft<T, R, DIR>(v[c]);
         const int d = ((j >> SLG) << (SLG + RLG)) + k;
