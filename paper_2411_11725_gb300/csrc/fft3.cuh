@@ -298,9 +298,11 @@ __device__ __forceinline__ void stage(Cx<T> *__restrict__ buf, int nl_rt, const 
         const int k = j & (NS - 1);
         if (NS > 1) {
             const int kk = k << sh;
-            if constexpr (R == 16) {
+            if constexpr (R == 16 && sizeof(T) == 4) {
                 // w^r for r < 16 from the four table values w, w^2, w^4, w^8 (four loads in flight together
-                // instead of fifteen; the other powers are at most three products away, a few roundings)
+                // instead of fifteen; the other powers are at most three products away, a few roundings).
+                // FP32 only: the FP64 passes are bound by the FP64 rate, where the products cost more than
+                // the loads they save.
                 Cx<T> w[16];
                 w[1] = tw[kk];
                 w[2] = tw[2 * kk];
