@@ -290,19 +290,28 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
     return f;
 }
 
+// Blocks of a node launch (1D grid): blocks b < full walk tile b over all node planes; the tiles after
+// them (the ones that would otherwise run alone in a last partial wave of long blocks) are split along z
+// into `chunks` blocks of zc planes each.  Tile t covers nodes x0 = (t % bxn) TX, y0 = (t / bxn) TY.
+struct NodeGrid {
+    int bxn, full, chunks, zc;
+};
+
 // STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
-// input.  Block (bx, by, bz) covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [bz*zc, bz*zc+zc).
+// input.  Each block covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [z0, z1) (NodeGrid).
 template <typename T, bool STAGE, bool DMI = false>
 __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(LocalParams<T> p, const T *__restrict__ y,
                                                         T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
-                                                        double t_heff, int zc)
+                                                        double t_heff, NodeGrid ng)
 {
     if (STAGE && sa.ctl && sa.ctl->done) return;
     constexpr int TY = kTY<T>;
     __shared__ NodeSmem<T> sm;
     const Geom &g = p.g;
-    const int x0 = blockIdx.x * kTX, y0 = blockIdx.y * TY;
-    const int z0 = blockIdx.z * zc, z1 = min(g.nn3, z0 + zc);
+    const int b = blockIdx.x, split = b >= ng.full;
+    const int tile = split ? ng.full + (b - ng.full) / ng.chunks : b;
+    const int z0 = split ? (b - ng.full) % ng.chunks * ng.zc : 0, z1 = split ? min(g.nn3, z0 + ng.zc) : g.nn3;
+    const int x0 = tile % ng.bxn * kTX, y0 = tile / ng.bxn * TY;
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const int n1 = x0 + tx, n2 = y0 + ty;
     const bool active = n1 < g.nn1 && n2 < g.nn2;
@@ -778,15 +787,33 @@ __global__ void __launch_bounds__(256) k_dmi(LocalParams<T> p, const T *__restri
     out[2 * ns + n] = -ez;
 }
 
-template <typename T>
-static dim3 node_grid(const Geom &g, int *zc)
+// Launch shape of a node kernel instance.  R = blocks the device holds at once (occupancy times SMs,
+// queried once per instance).  With T tiles, the first T - (T mod R) tiles make whole waves of full-depth
+// blocks; the remaining T mod R tiles are split along z into about R / (T mod R) chunks each, so that
+// the last wave is short instead of a full-length wave on a fraction of the SMs.  Fewer tiles than R:
+// every tile is split the same way.
+template <typename T, bool STAGE, bool DMI>
+static NodeGrid node_grid(const Geom &g, int *blocks)
 {
-    const int bx = div_up(g.nn1, kTX), by = div_up(g.nn2, kTY<T>);
-    const long bxy = (long)bx * by;
-    int chunks = (int)((4L * 152 + bxy - 1) / bxy);
+    static int resident = 0;
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_node<T, STAGE, DMI>, kTX * kTY<T>, 0);
+        resident = (sms > 0 && per_sm > 0) ? sms * per_sm : 4 * 152;
+    }
+    NodeGrid ng{};
+    ng.bxn = div_up(g.nn1, kTX);
+    const int tiles = ng.bxn * div_up(g.nn2, kTY<T>);
+    const int tail = tiles % resident;
+    ng.full = tiles - tail;
+    int chunks = tail > 0 ? resident / tail : 1;
     chunks = chunks < 1 ? 1 : (chunks > g.nn3 ? g.nn3 : chunks);
-    *zc = div_up(g.nn3, chunks);
-    return dim3(bx, by, div_up(g.nn3, *zc));
+    ng.zc = div_up(g.nn3, chunks);
+    ng.chunks = div_up(g.nn3, ng.zc);
+    *blocks = ng.full + tail * ng.chunks;
+    return ng;
 }
 
 template <typename T>
@@ -801,14 +828,15 @@ void launch_heff(const LocalParams<T> &p, const T *y, T *h_out, double t, cudaSt
         k_node1d<T, false><<<p.g.nn1, kNode1dThreads, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t);
         return;
     }
-    int zc;
-    const dim3 grid = node_grid<T>(p.g, &zc);
+    int nb;
     if (p.hdmi) {
+        const NodeGrid ng = node_grid<T, false, true>(p.g, &nb);
         k_dmi<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, p.hdmi);
-        k_node<T, false, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
+        k_node<T, false, true><<<nb, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, ng);
         return;
     }
-    k_node<T, false><<<grid, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, zc);
+    const NodeGrid ng = node_grid<T, false, false>(p.g, &nb);
+    k_node<T, false><<<nb, kTX * kTY<T>, 0, st>>>(p, y, h_out, nullptr, StageArgs{}, t, ng);
 }
 
 template <typename T>
@@ -823,14 +851,15 @@ void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, 
         k_node1d<T, true><<<p.g.nn1, kNode1dThreads, 0, st>>>(p, y, k_out, y_next, sa, 0.0);
         return;
     }
-    int zc;
-    const dim3 grid = node_grid<T>(p.g, &zc);
+    int nb;
     if (p.hdmi) {
+        const NodeGrid ng = node_grid<T, true, true>(p.g, &nb);
         k_dmi<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, p.hdmi);
-        k_node<T, true, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
+        k_node<T, true, true><<<nb, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, ng);
         return;
     }
-    k_node<T, true><<<grid, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, zc);
+    const NodeGrid ng = node_grid<T, true, false>(p.g, &nb);
+    k_node<T, true><<<nb, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, ng);
 }
 
 // ---------------------------------------------------------------------------------------------
