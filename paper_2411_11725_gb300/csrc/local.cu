@@ -29,22 +29,44 @@ template <typename T>
 constexpr int kTY = 4;  // 128-thread tiles, six FP32 blocks per SM at 80 registers (measured best of 32 x 2/4/8 tiles and 4-8 blocks)
 constexpr int kNodeSlots = 4, kCellSlots = 3;
 
-// a nodal or cell 3-vector in shared memory: padded to one 16-byte access in FP32, packed in FP64
+// a nodal or cell 3-vector
 template <typename T>
 struct V4 {
     T x, y, z;
 };
-template <>
-struct alignas(16) V4<float> {
-    float x, y, z, w;
+
+// NS rotating planes of R x C 3-vectors in shared memory.  FP64: packed triples.  FP32: x and y as one
+// 8-byte pair and z apart, 12 bytes per vector: a warp reads a row of vectors with one 8-byte and one
+// 4-byte shared load, three wavefronts instead of the four of a 16-byte padded vector (the node
+// kernel's shared-memory pipe is its busiest unit).
+template <typename T, int NS, int R, int C>
+struct Planes {
+    V4<T> v[NS][R][C];
+    __device__ __forceinline__ V4<T> get(int s, int r, int c) const { return v[s][r][c]; }
+    __device__ __forceinline__ T *px(int s, int r, int c) { return &v[s][r][c].x; }
+    __device__ __forceinline__ T *py(int s, int r, int c) { return &v[s][r][c].y; }
+    __device__ __forceinline__ T *pz(int s, int r, int c) { return &v[s][r][c].z; }
+};
+template <int NS, int R, int C>
+struct Planes<float, NS, R, C> {
+    float2 xy[NS][R][C];
+    float z[NS][R][C];
+    __device__ __forceinline__ V4<float> get(int s, int r, int c) const
+    {
+        const float2 a = xy[s][r][c];
+        return V4<float>{a.x, a.y, z[s][r][c]};
+    }
+    __device__ __forceinline__ float *px(int s, int r, int c) { return &xy[s][r][c].x; }
+    __device__ __forceinline__ float *py(int s, int r, int c) { return &xy[s][r][c].y; }
+    __device__ __forceinline__ float *pz(int s, int r, int c) { return &z[s][r][c]; }
 };
 
 template <typename T>
 struct NodeSmem {
     static constexpr int SX = kTX + 2, SY = kTY<T> + 2;  // node plane with halo
     static constexpr int CX = kTX + 1, CY = kTY<T> + 1;  // cell plane around the tile
-    V4<T> y[kNodeSlots][SY][SX];   // node plane z in slot (z + 4) % 4
-    V4<T> c[kCellSlots][CY][CX];   // cell plane c3 in slot (c3 + 3) % 3, Ms_c H_c
+    Planes<T, kNodeSlots, SY, SX> y;  // node plane z in slot (z + 4) % 4
+    Planes<T, kCellSlots, CY, CX> c;  // cell plane c3 in slot (c3 + 3) % 3, Ms_c H_c
     T hf[4];
 };
 
@@ -66,7 +88,7 @@ __device__ __forceinline__ void load_node_plane(const LocalParams<T> &p, const T
 {
     using S = NodeSmem<T>;
     const Geom &g = p.g;
-    V4<T>(*dst)[S::SX] = sm.y[(z + kNodeSlots) % kNodeSlots];
+    const int sl = (z + kNodeSlots) % kNodeSlots;
     const bool zin = z >= 0 && z < g.nn3;
     const int ns = (int)g.ns;
     for (int t = threadIdx.x; t < S::SX * S::SY; t += blockDim.x) {
@@ -74,9 +96,9 @@ __device__ __forceinline__ void load_node_plane(const LocalParams<T> &p, const T
         const int nx = x0 - 1 + cc, ny = y0 - 1 + r;
         const bool in = zin && nx >= 0 && nx < g.nn1 && ny >= 0 && ny < g.nn2;
         const int n = in ? (z * g.nn2 + ny) * g.nn1 + nx : 0;
-        cp_val(&dst[r][cc].x, y + n, in);
-        cp_val(&dst[r][cc].y, y + ns + n, in);
-        cp_val(&dst[r][cc].z, y + 2 * ns + n, in);
+        cp_val(sm.y.px(sl, r, cc), y + n, in);
+        cp_val(sm.y.py(sl, r, cc), y + ns + n, in);
+        cp_val(sm.y.pz(sl, r, cc), y + 2 * ns + n, in);
     }
 }
 
@@ -86,7 +108,7 @@ __device__ __forceinline__ void load_cell_plane(const LocalParams<T> &p, NodeSme
     using S = NodeSmem<T>;
     const Geom &g = p.g;
     if (!p.MsH || !(p.terms & NM_DEMAG)) return;  // the cell planes are not read
-    V4<T>(*dst)[S::CX] = sm.c[(c3 + kCellSlots) % kCellSlots];
+    const int sl = (c3 + kCellSlots) % kCellSlots;
     const bool zin = c3 >= 0 && c3 < g.N3;
     const int cs = (int)g.cs;
     for (int t = threadIdx.x; t < S::CX * S::CY; t += blockDim.x) {
@@ -94,9 +116,9 @@ __device__ __forceinline__ void load_cell_plane(const LocalParams<T> &p, NodeSme
         const int c1 = x0 - 1 + cc, c2 = y0 - 1 + r;
         const bool in = zin && c1 >= 0 && c1 < g.N1 && c2 >= 0 && c2 < g.N2;
         const int c = in ? (c3 * g.N2 + c2) * g.N1 + c1 : 0;
-        cp_val(&dst[r][cc].x, p.MsH + c, in);
-        cp_val(&dst[r][cc].y, p.MsH + cs + c, in);
-        cp_val(&dst[r][cc].z, p.MsH + 2 * cs + c, in);
+        cp_val(sm.c.px(sl, r, cc), p.MsH + c, in);
+        cp_val(sm.c.py(sl, r, cc), p.MsH + cs + c, in);
+        cp_val(sm.c.pz(sl, r, cc), p.MsH + 2 * cs + c, in);
     }
 }
 
@@ -123,7 +145,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
     const int cx0 = tx + 1, cy0 = ty + 1;
     NodeField<T> f;
     {
-        const V4<T> m = sm.y[sz0][cy0][cx0];
+        const V4<T> m = sm.y.get(sz0, cy0, cx0);
         f.mx = m.x;
         f.my = m.y;
         f.mz = m.z;
@@ -141,7 +163,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 #pragma unroll
                 for (int o1 = -1; o1 <= 1; ++o1) {
                     const int k = (o3 + 1) * 9 + (o2 + 1) * 3 + (o1 + 1);
-                    const V4<T> q = sm.y[slot][cy0 + o2][cx0 + o1];
+                    const V4<T> q = sm.y.get(slot, cy0 + o2, cx0 + o1);
                     if (k != 13) {
                         sx += p.wex27[k] * q.x;
                         sy += p.wex27[k] * q.y;
@@ -174,7 +196,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
                     const int cnt = k23 * (o1 < 0 ? cm1 : (o1 > 0 ? cp1 : cm1 + cp1));
                     const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
                     const T fc = (T)cnt;
-                    const V4<T> q = sm.y[slot][cy0 + o2][cx0 + o1];
+                    const V4<T> q = sm.y.get(slot, cy0 + o2, cx0 + o1);
                     if (d != 0) {
                         const T w = p.wexd[d] * fc;
                         sx += w * q.x;
@@ -226,7 +248,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
                     }
                     const int d = ((o1 != 0) << 2) | ((o2 != 0) << 1) | (o3 != 0);
                     const bool self = (o1 == 0 && o2 == 0 && o3 == 0);
-                    const V4<T> q = sm.y[slot][cy0 + o2][cx0 + o1];
+                    const V4<T> q = sm.y.get(slot, cy0 + o2, cx0 + o1);
                     if (!self) {
                         const T w = p.Wex[d] * S;
                         ex += w * (q.x - f.mx);
@@ -247,7 +269,7 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int i1 = (i >> 2) & 1, i2 = (i >> 1) & 1, i3 = i & 1;
-            const V4<T> v = sm.c[(n3 - i3 + kCellSlots) % kCellSlots][cy0 - i2][cx0 - i1];
+            const V4<T> v = sm.c.get((n3 - i3 + kCellSlots) % kCellSlots, cy0 - i2, cx0 - i1);
             cx_ += v.x;
             cy_ += v.y;
             cz_ += v.z;
