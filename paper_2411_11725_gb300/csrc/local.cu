@@ -312,6 +312,14 @@ __device__ __forceinline__ NodeField<T> node_field(const LocalParams<T> &p, cons
     return f;
 }
 
+// FP32 stage kernels that form the next stage input from three or more earlier slopes stage each node's
+// own values one plane ahead in shared memory, beside the node and cell planes: 1/mass, the earlier
+// slopes with non-zero coefficients and the FP32 copy of m.  Their global loads then have a whole plane
+// of work to arrive in, instead of stalling the stage-input sums (with fewer slopes the extra copies
+// cost more than the stalls they remove).  Every Runge-Kutta tableau of the library has at most
+// kOwnSlopes such slopes per stage.
+constexpr int kOwnSlopes = 4, kOwnVals = 1 + 3 * kOwnSlopes + 3;
+
 // Blocks of a node launch (1D grid): blocks b < full walk tile b over all node planes; the tiles after
 // them (the ones that would otherwise run alone in a last partial wave of long blocks) are split along z
 // into `chunks` blocks of zc planes each.  Tile t covers nodes x0 = (t % bxn) TX, y0 = (t / bxn) TY.
@@ -321,14 +329,18 @@ struct NodeGrid {
 
 // STAGE = false: write H (effective-field evaluation); true: write the LLG slope k_s and the next stage
 // input.  Each block covers nodes x0.. x0+TX-1, y0.. y0+TY-1 and z in [z0, z1) (NodeGrid).
-template <typename T, bool STAGE, bool DMI = false>
+// OWN (FP32 stage kernels with a next stage input from the FP32 copy of m and at most kOwnSlopes
+// earlier slopes): the node's own values are staged in shared memory.
+template <typename T, bool STAGE, bool DMI = false, bool OWN = false>
 __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(LocalParams<T> p, const T *__restrict__ y,
                                                         T *__restrict__ out, T *__restrict__ y_next, StageArgs sa,
                                                         double t_heff, NodeGrid ng)
 {
+    static_assert(!OWN || (sizeof(T) == 4 && STAGE && !DMI), "own-value staging is for FP32 stage kernels");
     if (STAGE && sa.ctl && sa.ctl->done) return;
     constexpr int TY = kTY<T>;
     __shared__ NodeSmem<T> sm;
+    __shared__ float own_sm[OWN ? 2 : 1][OWN ? kOwnVals : 1][TY][kTX];
     const Geom &g = p.g;
     const int b = blockIdx.x, split = b >= ng.full;
     const int tile = split ? ng.full + (b - ng.full) / ng.chunks : b;
@@ -337,6 +349,28 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
     const int tx = threadIdx.x % kTX, ty = threadIdx.x / kTX;
     const int n1 = x0 + tx, n2 = y0 + ty;
     const bool active = n1 < g.nn1 && n2 < g.nn2;
+    // OWN: copy node plane zz's own values of this thread into slot zz & 1
+    auto load_own = [&](int zz) {
+        if constexpr (OWN) {
+            const int nq = (zz * g.nn2 + n2) * g.nn1 + n1, nsq = (int)g.ns;
+            float(*o)[TY][kTX] = own_sm[zz & 1];
+            cp_val(&o[0][ty][tx], (const float *)p.inv_mass + nq, true);
+            int q = 1;
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                if (j + 1 >= sa.s) break;
+                if (sa.af[j] == 0.f) continue;
+                const float *kj = (const float *)sa.k[j];
+                cp_val(&o[q][ty][tx], kj + nq, true);
+                cp_val(&o[q + 1][ty][tx], kj + nsq + nq, true);
+                cp_val(&o[q + 2][ty][tx], kj + 2 * nsq + nq, true);
+                q += 3;
+            }
+            cp_val(&o[kOwnVals - 3][ty][tx], sa.mf + nq, true);
+            cp_val(&o[kOwnVals - 2][ty][tx], sa.mf + nsq + nq, true);
+            cp_val(&o[kOwnVals - 1][ty][tx], sa.mf + 2 * nsq + nq, true);
+        }
+    };
     if (threadIdx.x == 0) {
         const double t = STAGE ? (sa.ctl ? sa.ctl->t + sa.c_s * sa.ctl->dt : sa.t_fixed) : t_heff;
         const double su = time_factor<T>(p.hu_freq, p.hu_phase, t);
@@ -352,6 +386,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     load_node_plane(p, y, sm, z0 + 1, x0, y0);
     load_cell_plane(p, sm, z0, x0, y0);
+    if (OWN && active) load_own(z0);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     const int ns = (int)g.ns;
     double dt = 0.0;
@@ -365,6 +400,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
         if (z + 1 < z1) {
             load_node_plane(p, y, sm, z + 2, x0, y0);
             load_cell_plane(p, sm, z + 1, x0, y0);
+            if (OWN && active) load_own(z + 1);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
         // this node's own values (1/mass; for the next stage input, the earlier slopes and the FP32 copy
@@ -378,7 +414,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
             dmy = p.hdmi[ns + n];
             dmz = p.hdmi[2 * ns + n];
         }
-        if (active) {
+        if (!OWN && active) {
             im = p.inv_mass[n];
             if (STAGE && y_next) {
 #pragma unroll
@@ -401,6 +437,9 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
         asm volatile("cp.async.wait_group 1;\n" ::: "memory");
         __syncthreads();
         const bool interior = tile_inner && z >= 1 && z <= g.N3 - 1;
+        if constexpr (OWN) {
+            if (active) im = (T)own_sm[z & 1][0][ty][tx];
+        }
         if (active) {
             NodeField<T> f = interior    ? node_field<T, 1>(p, sm, n1, n2, z, im, tx, ty)
                              : p.uniform ? node_field<T, 2>(p, sm, n1, n2, z, im, tx, ty)
@@ -436,6 +475,24 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
                 if (y_next) {
                     // y_{s+1} = m + dt sum_{j<=s} a_{s+1,j} k_j: the slope combination in the working
                     // precision
+                    if constexpr (OWN) {
+                        // the earlier slopes and the FP32 copy of m from the staged own values
+                        const float(*o)[TY][kTX] = own_sm[z & 1];
+                        int q = 1;
+#pragma unroll
+                        for (int j = 0; j < 7; ++j) {
+                            if (j + 1 >= sa.s) break;
+                            const float aj = sa.af[j];
+                            if (aj == 0.f) continue;
+                            px += aj * o[q][ty][tx];
+                            py += aj * o[q + 1][ty][tx];
+                            pz += aj * o[q + 2][ty][tx];
+                            q += 3;
+                        }
+                        mfx = o[kOwnVals - 3][ty][tx];
+                        mfy = o[kOwnVals - 2][ty][tx];
+                        mfz = o[kOwnVals - 1][ty][tx];
+                    }
                     const T as = sizeof(T) == 4 ? (T)sa.af_s : (T)sa.a_s;
                     const T ax = px + as * kx, ay = py + as * ky, az = pz + as * kz;
                     if (sizeof(T) == 4 && sa.mf) {
@@ -814,7 +871,7 @@ __global__ void __launch_bounds__(256) k_dmi(LocalParams<T> p, const T *__restri
 // blocks; the remaining T mod R tiles are split along z into about R / (T mod R) chunks each, so that
 // the last wave is short instead of a full-length wave on a fraction of the SMs.  Fewer tiles than R:
 // every tile is split the same way.
-template <typename T, bool STAGE, bool DMI>
+template <typename T, bool STAGE, bool DMI, bool OWN = false>
 static NodeGrid node_grid(const Geom &g, int *blocks)
 {
     static int resident = 0;
@@ -822,7 +879,7 @@ static NodeGrid node_grid(const Geom &g, int *blocks)
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_node<T, STAGE, DMI>, kTX * kTY<T>, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_node<T, STAGE, DMI, OWN>, kTX * kTY<T>, 0);
         resident = (sms > 0 && per_sm > 0) ? sms * per_sm : 4 * 152;
     }
     NodeGrid ng{};
@@ -879,6 +936,21 @@ void launch_llg_stage(const LocalParams<T> &p, const T *y, T *k_out, T *y_next, 
         k_dmi<T><<<div_up(p.g.n_nodes, 256), 256, 0, st>>>(p, y, p.hdmi);
         k_node<T, true, true><<<nb, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, ng);
         return;
+    }
+    if constexpr (sizeof(T) == 4) {
+        int n_earlier = 0;  // earlier slopes with non-zero coefficients in the next stage input
+        for (int j = 0; j + 1 < sa.s && j < 7; ++j) n_earlier += sa.af[j] != 0.f;
+        if (y_next && sa.mf && n_earlier >= 3 && n_earlier <= kOwnSlopes) {
+            static bool carveout = false;  // six 32 KB blocks per SM: ask for the largest shared carveout
+            if (!carveout) {
+                cudaFuncSetAttribute((const void *)k_node<float, true, false, true>,
+                                     cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+                carveout = true;
+            }
+            const NodeGrid ng = node_grid<T, true, false, true>(p.g, &nb);
+            k_node<T, true, false, true><<<nb, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, ng);
+            return;
+        }
     }
     const NodeGrid ng = node_grid<T, true, false>(p.g, &nb);
     k_node<T, true><<<nb, kTX * kTY<T>, 0, st>>>(p, y, k_out, y_next, sa, 0.0, ng);
