@@ -46,6 +46,10 @@ struct Planes {
     __device__ __forceinline__ T *px(int s, int r, int c) { return &v[s][r][c].x; }
     __device__ __forceinline__ T *py(int s, int r, int c) { return &v[s][r][c].y; }
     __device__ __forceinline__ T *pz(int s, int r, int c) { return &v[s][r][c].z; }
+    // element t of plane s in row-major order
+    __device__ __forceinline__ T *px(int s, int t) { return &(&v[s][0][0])[t].x; }
+    __device__ __forceinline__ T *py(int s, int t) { return &(&v[s][0][0])[t].y; }
+    __device__ __forceinline__ T *pz(int s, int t) { return &(&v[s][0][0])[t].z; }
 };
 template <int NS, int R, int C>
 struct Planes<float, NS, R, C> {
@@ -59,6 +63,9 @@ struct Planes<float, NS, R, C> {
     __device__ __forceinline__ float *px(int s, int r, int c) { return &xy[s][r][c].x; }
     __device__ __forceinline__ float *py(int s, int r, int c) { return &xy[s][r][c].y; }
     __device__ __forceinline__ float *pz(int s, int r, int c) { return &z[s][r][c]; }
+    __device__ __forceinline__ float *px(int s, int t) { return &(&xy[s][0][0])[t].x; }
+    __device__ __forceinline__ float *py(int s, int t) { return &(&xy[s][0][0])[t].y; }
+    __device__ __forceinline__ float *pz(int s, int t) { return &z[s][0][0] + t; }
 };
 
 template <typename T>
@@ -82,23 +89,49 @@ __device__ __forceinline__ void cp_val(T *dst, const T *src, bool in)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 
+// What one thread copies of every node plane: elements t = threadIdx.x and threadIdx.x + TX TY of the
+// plane's row-major halo layout, each with its in-plane offset in the node array, or -1 where it lies
+// outside the mesh (zero fill).  The same for every z: formed once per tile.
+struct PlaneCopy {
+    int node[2];
+};
+
 template <typename T>
-__device__ __forceinline__ void load_node_plane(const LocalParams<T> &p, const T *__restrict__ y, NodeSmem<T> &sm,
-                                                int z, int x0, int y0)
+__device__ __forceinline__ PlaneCopy plane_copy(const Geom &g, int x0, int y0)
 {
     using S = NodeSmem<T>;
+    constexpr int NT = kTX * kTY<T>;
+    PlaneCopy pc;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int t = threadIdx.x + k * NT;
+        const int r = t / S::SX, cc = t - r * S::SX;
+        const int nx = x0 - 1 + cc, ny = y0 - 1 + r;
+        pc.node[k] = (nx >= 0 && nx < g.nn1 && ny >= 0 && ny < g.nn2) ? ny * g.nn1 + nx : -1;
+    }
+    return pc;
+}
+
+template <typename T>
+__device__ __forceinline__ void load_node_plane(const LocalParams<T> &p, const T *__restrict__ y, NodeSmem<T> &sm,
+                                                int z, const PlaneCopy &pc)
+{
+    using S = NodeSmem<T>;
+    constexpr int NT = kTX * kTY<T>;
     const Geom &g = p.g;
     const int sl = (z + kNodeSlots) % kNodeSlots;
     const bool zin = z >= 0 && z < g.nn3;
-    const int ns = (int)g.ns;
-    for (int t = threadIdx.x; t < S::SX * S::SY; t += blockDim.x) {
-        const int r = t / S::SX, cc = t - r * S::SX;
-        const int nx = x0 - 1 + cc, ny = y0 - 1 + r;
-        const bool in = zin && nx >= 0 && nx < g.nn1 && ny >= 0 && ny < g.nn2;
-        const int n = in ? (z * g.nn2 + ny) * g.nn1 + nx : 0;
-        cp_val(sm.y.px(sl, r, cc), y + n, in);
-        cp_val(sm.y.py(sl, r, cc), y + ns + n, in);
-        cp_val(sm.y.pz(sl, r, cc), y + 2 * ns + n, in);
+    const int ns = (int)g.ns, zo = z * g.nn2 * g.nn1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int t = threadIdx.x + k * NT;
+        if (t < S::SX * S::SY) {
+            const bool in = zin && pc.node[k] >= 0;
+            const int n = in ? zo + pc.node[k] : 0;
+            cp_val(sm.y.px(sl, t), y + n, in);
+            cp_val(sm.y.py(sl, t), y + ns + n, in);
+            cp_val(sm.y.pz(sl, t), y + 2 * ns + n, in);
+        }
     }
 }
 
@@ -379,12 +412,13 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
         sm.hf[2] = (T)(p.hu2 * su);
         sm.hf[3] = (T)time_factor<T>(p.hc_freq, p.hc_phase, t);
     }
+    const PlaneCopy pc = plane_copy<T>(g, x0, y0);
     // copy groups: {node z0-1, node z0, cell z0-1}, then per z the group {node z+1, cell z}
-    load_node_plane(p, y, sm, z0 - 1, x0, y0);
-    load_node_plane(p, y, sm, z0, x0, y0);
+    load_node_plane(p, y, sm, z0 - 1, pc);
+    load_node_plane(p, y, sm, z0, pc);
     load_cell_plane(p, sm, z0 - 1, x0, y0);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
-    load_node_plane(p, y, sm, z0 + 1, x0, y0);
+    load_node_plane(p, y, sm, z0 + 1, pc);
     load_cell_plane(p, sm, z0, x0, y0);
     if (OWN && active) load_own(z0);
     asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -398,7 +432,7 @@ __global__ void __launch_bounds__(kTX *kTY<T>, sizeof(T) == 4 ? 6 : 3) k_node(Lo
         // start the copies for the next plane (into the slots of planes z - 2 and cells z - 2, free since
         // the barrier that ended the previous iteration), then wait for everything but them
         if (z + 1 < z1) {
-            load_node_plane(p, y, sm, z + 2, x0, y0);
+            load_node_plane(p, y, sm, z + 2, pc);
             load_cell_plane(p, sm, z + 1, x0, y0);
             if (OWN && active) load_own(z + 1);
         }
