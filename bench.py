@@ -808,10 +808,11 @@ def serving_kwargs(i, p):
                 atol=p.extra["atol"], dt0=p.extra["dt0"], tag=i)
 
 
-def run_serving(n_requests, budget_bytes, max_active, loads=(0.7, 1.2), n_capacity=8):
+def run_serving(n_requests, budget_bytes, max_active, loads=(0.7, 1.2, 8.0), n_capacity=8):
     """Poisson streams of mixed-size LLG runs through the library's request loop.  Capacity = 1 / mean
     service time of runs executed one at a time; each load level replays the same requests with arrival
-    rate = load x capacity.  Latency = submit -> result on the host."""
+    rate = load x capacity.  Latency = submit -> result on the host.  The 8x level keeps the queue full:
+    its throughput is the ceiling of the request loop with up to max_active runs on the GPU at once."""
     from paper_2411_11725_gb300.serve import Server, replay
     reqs = inp.serving_requests(max(n_requests, n_capacity), seed=0, rate_hz=1.0)
     stream = [(t, serving_kwargs(i, p)) for i, (t, p) in enumerate(reqs[:n_requests])]
