@@ -3,6 +3,8 @@
 // never materialised: every pass reads only the non-zero part of its input and writes only the part
 // of its output that later passes use.
 #pragma once
+#include <cuda.h>  // CUtensorMap (descriptor type only; the encoder is reached through the runtime)
+
 #include "nm_common.cuh"
 
 namespace nm {
@@ -37,6 +39,10 @@ struct DemagBufs {
     T Ms0;
     const StepCtl *ctl;        // when set, passes do nothing once ctl->done (finished integrations)
     Marker mark;               // profiling hook
+    // TMA descriptor of the inverse y pass over S (host copy, passed to the kernel by value; built
+    // once per mesh by demag_encode_ymap)
+    const CUtensorMap *ymap_inv = nullptr;
+    int *wait_err = nullptr;   // device status word set to NM_ERR_TIMEOUT when a bounded wait runs out
 };
 
 // Launch shapes of the passes (lines per block bounded by the FFT engine's 16 values per thread).
@@ -53,6 +59,7 @@ struct DemagPlan {
     bool z_reg;                // FP32, P3 <= 64: the register z convolution (two threads per line)
     int yc_G, yc_threads;
     size_t yc_smem;
+    size_t yi_smem;            // inverse y pass (TMA tile: alignment slack and barrier)
 };
 template <typename T>
 DemagPlan demag_plan(const Geom &g);
@@ -65,6 +72,11 @@ void demag_forward(const Geom &g, const DemagBufs<T> &b, const T *y, T *MsH, cud
 // replaces the node->cell averaging; output H (3 x cs) without the Ms factor.  Used by the adjoint.
 template <typename T>
 void demag_cells(const Geom &g, const DemagBufs<T> &b, const T *M, T *H, cudaStream_t st);
+
+// TMA descriptor of the inverse y pass over the spectrum buffer S (host work only; no device access).
+// Returns 0, or a non-zero code when the driver's encoder is unavailable or refuses the shape.
+template <typename T>
+int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *inv);
 
 // Raise the dynamic shared-memory limit of every demag kernel once (outside any graph capture).
 void demag_init_attributes();

@@ -17,5 +17,6 @@ void demag_init_attributes()
 template DemagPlan demag_plan<float>(const Geom &);
 template void demag_forward<float>(const Geom &, const DemagBufs<float> &, const float *, float *, cudaStream_t);
 template void demag_cells<float>(const Geom &, const DemagBufs<float> &, const float *, float *, cudaStream_t);
+template int demag_encode_ymap<float>(const Geom &, void *, CUtensorMap *);
 
 }  // namespace nm

@@ -6,13 +6,16 @@
 //
 // Every kernel is instantiated per log2 transform length (the f3 engine), so the index arithmetic of
 // the FFT stages is resolved at compile time.  The x passes read their input in the first FFT stage
-// straight from global memory (the zero padding is never read); the y and z passes stage their strided
-// tiles in shared memory with cp.async (all copies of a tile in flight at once).  Every pass writes its
+// straight from global memory (the zero padding is never read); the forward y pass and the z passes
+// stage their strided tiles in shared memory with cp.async (all copies of a tile in flight at once), the
+// inverse y pass with one TMA tensor copy per tile.  Every pass writes its
 // output from the last FFT stage straight to global memory, and only the part that later passes read.
 //
 // Templates only: demag_f32.cu and demag_f64.cu instantiate them (two translation units, compiled in
 // parallel).
 #pragma once
+#include <string.h>
+
 #include "demag.cuh"
 #include "fft3.cuh"
 
@@ -68,8 +71,11 @@ struct YTile {
     static constexpr int G = G0 > 16 ? 16 : (G0 < 1 ? 1 : G0);
     static constexpr int LFP = G < 16 ? 3 : 0;
     static constexpr int THREADS = ((G * P2 / EPT > 32 ? G * P2 / EPT : 32) + 31) / 32 * 32;
-    static constexpr size_t SMEM = (size_t)G * f3::lf_rows(P2, LFP) * sizeof(Cx<T>);
+    static constexpr size_t SMEM = (size_t)G * f3::lf_rows(P2, LFP) * sizeof(Cx<T>), TILE_BYTES = SMEM;
+    // inverse pass: the tile, up to 128 bytes to align it for the TMA copy, and the copy's barrier
+    static constexpr size_t SMEM_TMA = TILE_BYTES + 128 + 16;
     static_assert(G * P2 <= EPT * THREADS && THREADS <= MAXT, "y tile exceeds the block");
+    static_assert(TILE_BYTES % 8 == 0, "barrier alignment");
 };
 
 // x passes: radix-16 stages for FP32 lines of 2^10 complex values
@@ -305,18 +311,81 @@ __global__ void k_x_inv1(Geom g, DemagBufs<T> b, T *__restrict__ out)
     out[xi.in] = v;
 }
 
+// Shared-memory barriers and TMA tile copies (cp.async.bulk.tensor): one thread issues the copy of a
+// block's whole tile, which completes on an mbarrier with its byte count; the threads wait on the
+// barrier's phase.  Every wait is bounded (about a second of SM clock): a wait that runs out reports
+// NM_ERR_TIMEOUT through the status word and the block writes nothing.
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (unsigned it = 0; it < (1u << 26); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (clock64() - t0 > (2LL << 30)) break;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *tm, int c0, int c1, int c2, unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(dst),
+        "l"((unsigned long long)tm), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *tm, int c0, int c1, int c2, int c3,
+                                            unsigned bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5}], [%6];\n" ::"r"(dst),
+        "l"((unsigned long long)tm), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
+
+// Bytes of the inverse y pass's TMA tile copy (all P2 rows): groups of 8 rows plus the zero-filled
+// padding row when the tile pads its rows (LFP = 3), plain rows otherwise (the box of demag_encode_ymap)
+template <typename T, int LG>
+__host__ __device__ constexpr unsigned y_tile_bytes()
+{
+    constexpr unsigned rowb = YTile<T, LG>::G * (unsigned)sizeof(Cx<T>), rows = 1u << LG;
+    return YTile<T, LG>::LFP > 0 ? rows / 8 * 9u * rowb : rows * rowb;
+}
+
 // Passes 2 and 4: y transform of G consecutive kx columns of one (component, z) plane, in place.
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
 // Shared layout: row y at buf + lfpad(y) * G (lines = columns, fastest; padded rows for narrow tiles).
-template <typename T, int LG, int DIR>
-__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geom g, DemagBufs<T> b)
+//
+// Forward y pass: the N2 input rows of the tile staged with cp.async (all copies in flight at once).
+// (A TMA copy of the same box was measured slower here: 0.693 against 0.674 ms at 1024x1024x32.)
+template <typename T, int LG>
+__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y_fwd(Geom g, DemagBufs<T> b)
 {
     if (b.ctl && b.ctl->done) return;
     constexpr int P2 = 1 << LG, G = YTile<T, LG>::G, LFP = YTile<T, LG>::LFP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
     Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
-    const int nin = DIR < 0 ? g.N2 : P2, nout = DIR < 0 ? P2 : g.N2;
+    const int nin = g.N2, nout = P2;
     const int Xp = g.Xp;
     constexpr int rowb = G * (int)sizeof(Cx<T>);
     constexpr int cb = rowb >= 16 ? 16 : rowb;
@@ -328,8 +397,45 @@ __global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y(Geo
     cpa_wait_all();
     __syncthreads();
     auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    f3::fft<T, LG, DIR, true, true, false, kYEpt<T, LG>, G, LFP>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, nout,
-                                                                 f3::NoFn<T>(), dst);
+    f3::fft<T, LG, -1, true, true, false, kYEpt<T, LG>, G, LFP>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, nout,
+                                                                f3::NoFn<T>(), dst);
+}
+
+// Inverse y pass: the whole P2-row tile arrives by one TMA copy (descriptor tm, built by
+// demag_encode_ymap) that completes on a shared-memory barrier.  With padded rows the copy's box spans
+// 9 rows of each group of 8, the ninth outside the tensor and zero-filled by the copy, so the box lands
+// in the padded layout as it is.  0.610 against 0.658 ms with cp.async staging at 1024x1024x32.
+template <typename T, int LG>
+__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>)
+    k_y_inv(Geom g, DemagBufs<T> b, const __grid_constant__ CUtensorMap tm)
+{
+    if (b.ctl && b.ctl->done) return;
+    constexpr int G = YTile<T, LG>::G, LFP = YTile<T, LG>::LFP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // the tile at the first 128-byte boundary of the dynamic buffer, the barrier behind it
+    const unsigned pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
+    Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw + pad);
+    const unsigned bar = smem_u32(smem_raw + pad + YTile<T, LG>::TILE_BYTES);
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, y_tile_bytes<T, LG>());
+        const int x0 = 2 * G * blockIdx.x;  // real elements: a multiple of 2G, i.e. of 16 bytes
+        if constexpr (LFP > 0) tma_load_4d(smem_u32(buf), &tm, x0, 0, 0, blockIdx.y, bar);
+        else tma_load_3d(smem_u32(buf), &tm, x0, 0, blockIdx.y, bar);
+    }
+    const bool arrived = mbar_wait_bounded(bar, 0);
+    if (__syncthreads_or(!arrived)) {
+        if (threadIdx.x == 0 && b.wait_err) atomicExch(b.wait_err, NM_ERR_TIMEOUT);
+        mbar_wait_bounded(bar, 0);  // the copy may still land: let it finish before the block exits
+        return;
+    }
+    constexpr int P2 = 1 << LG;
+    Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
+    const int Xp = g.Xp;
+    auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
+    f3::fft<T, LG, +1, true, true, false, kYEpt<T, LG>, G, LFP>(buf, G, FastDiv(1u), b.tw, g.twlg, P2, g.N2,
+                                                                f3::NoFn<T>(), dst);
 }
 
 // The six real tensor components at octant frequency (kx, a2, kz), with the sign of the odd ones in
@@ -724,8 +830,8 @@ static void init_attributes_t()
     });
     f3::lg_for_each<1, 11>([&](auto c) {
         constexpr int LG = decltype(c)::value;
-        set_smem((const void *)k_y<T, LG, -1>);
-        set_smem((const void *)k_y<T, LG, +1>);
+        set_smem((const void *)k_y_fwd<T, LG>);
+        set_smem((const void *)k_y_inv<T, LG>);
     });
     f3::lg_for_each<1, 7>([&](auto c) {
         constexpr int LG = decltype(c)::value;
@@ -795,6 +901,7 @@ DemagPlan demag_plan(const Geom &g)
             p.y_G = Y::G;
             p.y_threads = Y::THREADS;
             p.y_smem = Y::SMEM;
+            p.yi_smem = Y::SMEM_TMA;
         });
         if (g.lgP3 < 1 || g.lgP3 > 7) p.ok = false;
         f3::lg_dispatch<1, 7>(g.lgP3, [&](auto c) {
@@ -838,9 +945,64 @@ DemagPlan demag_plan(const Geom &g)
     // the kx grouping divides Xp (a multiple of 16)
     const int Gmax = g.N3 > 1 ? (p.y_G > p.z_G ? p.y_G : p.z_G) : p.yc_G;
     if (g.Xp % Gmax != 0) p.ok = false;
-    if (p.x_smem > 200 * 1024 || p.xi_smem > 200 * 1024 || p.y_smem > 200 * 1024 || p.z_smem > 200 * 1024 || p.yc_smem > 200 * 1024)
+    if (p.x_smem > 200 * 1024 || p.xi_smem > 200 * 1024 || p.y_smem > 200 * 1024 || p.yi_smem > 200 * 1024 ||
+        p.z_smem > 200 * 1024 || p.yc_smem > 200 * 1024)
         p.ok = false;
     return p;
+}
+
+// ---------------------------------------------------------------------------------------------
+// TMA descriptor of the inverse y pass over S = [3][N3][P2][Xp] complex: every (component, z) plane
+// holds P2 rows of Xp complex values (rows of Xp * sizeof(Cx<T>) bytes, a multiple of 128).  Dimensions
+// in real elements, innermost first: the 2 Xp reals of a row, then (LFP = 3) the row within its group of
+// 8 and the group, or (LFP = 0) the row, then the 3 N3 planes.  The box is the 2G reals of a block's G kx
+// columns by all P2 rows of one plane: P2 / 8 groups of 9 rows (the ninth outside the tensor and
+// zero-filled: the padding row of the shared layout), or P2 plain rows.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled_fn()
+{
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return (EncodeTiledFn) nullptr;
+        return (EncodeTiledFn)f;
+    }();
+    return fn;
+}
+
+template <typename T>
+int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *inv)
+{
+    memset(inv, 0, sizeof(CUtensorMap));
+    if (g.N3 <= 1 || g.P2 <= 1) return 0;  // no y passes
+    const EncodeTiledFn enc = encode_tiled_fn();
+    if (!enc) return -1;
+    const DemagPlan p = demag_plan<T>(g);
+    if (!p.ok) return -1;
+    int LFP = 0;
+    f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) { LFP = YTile<T, decltype(c)::value>::LFP; });
+    const CUtensorMapDataType dt = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+    const cuuint64_t rowb = (cuuint64_t)g.Xp * sizeof(Cx<T>);
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    CUresult r;
+    if (LFP > 0) {
+        const cuuint64_t dims[4] = {(cuuint64_t)2 * g.Xp, 8, (cuuint64_t)g.P2 / 8, (cuuint64_t)3 * g.N3};
+        const cuuint64_t strides[3] = {rowb, 8 * rowb, (cuuint64_t)g.P2 * rowb};
+        const cuuint32_t box[4] = {(cuuint32_t)(2 * p.y_G), 9, (cuuint32_t)(g.P2 / 8), 1};
+        r = enc(inv, dt, 4, S, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        const cuuint64_t dims[3] = {(cuuint64_t)2 * g.Xp, (cuuint64_t)g.P2, (cuuint64_t)3 * g.N3};
+        const cuuint64_t strides[2] = {rowb, (cuuint64_t)g.P2 * rowb};
+        const cuuint32_t box[3] = {(cuuint32_t)(2 * p.y_G), (cuuint32_t)g.P2, 1};
+        r = enc(inv, dt, 3, S, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
 template <typename T, bool CELL>
@@ -848,6 +1010,8 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
 {
     const DemagPlan p = demag_plan<T>(g);
     if (!p.ok) return;
+    // (create_mesh refuses shapes without a plan or, where there are y passes, without their descriptors)
+    if (g.N3 > 1 && g.P2 > 1 && !b.ymap_inv) return;
     const int nlines = 3 * g.N2 * g.N3;
     if (g.P1 == 1) {
         k_x_fwd1<T, CELL><<<div_up(nlines, 256), 256, 0, st>>>(g, b, in);
@@ -862,7 +1026,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
                 constexpr int LG = decltype(c)::value;
-                k_y<T, LG, -1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b);
+                k_y_fwd<T, LG><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b);
             });
             b.mark("demag_y_fwd");
         }
@@ -884,7 +1048,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
                 constexpr int LG = decltype(c)::value;
-                k_y<T, LG, +1><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b);
+                k_y_inv<T, LG><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.yi_smem, st>>>(g, b, *b.ymap_inv);
             });
             b.mark("demag_y_inv");
         }

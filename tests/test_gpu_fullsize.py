@@ -182,3 +182,34 @@ def test_fp32_dense_random_state_matches_fp64_path(nmgb, terms_name):
         torch.cuda.empty_cache()
     err = (torch.linalg.vector_norm(out[0] - out[1]) / torch.linalg.vector_norm(out[1])).item()
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("n", [(256, 256, 8), (512, 512, 16)])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_sparse_demag_at_sweep_sizes(nmgb, sampled, precision, n):
+    """The throughput sweep's smaller cuboids instantiate the y passes at 512- and 1024-point lines
+    (8 or 4 kx columns per tile, padded tile rows) and the z convolution at 16 and 32 points, which the
+    small meshes and the 1024x1024 meshes above do not: a sparse source (a 2x2x2 node block at a corner
+    and one interior node) against the oracle's direct sum at nodes next to the sources and far away."""
+    import torch
+    p = _problem(n)
+    z = n[2]
+    src = (int(0.68 * n[0]), int(0.29 * n[1]), int(0.6 * z))
+    rng = np.random.default_rng(5)
+    m = np.zeros(p.nodes + (3,))
+    for nd in [(1, 1, 1), (2, 1, 1), (1, 2, 1), (2, 2, 1), (1, 1, 2), (2, 1, 2), (1, 2, 2), (2, 2, 2), src]:
+        m[nd] = inp.unit_vector(rng)
+    m = rounded(m, precision)
+    near = [(a, b, c) for a in (0, 2, 4) for b in (0, 2, 3) for c in (0, 1, 3)]
+    near += [(src[0] + a, src[1] + b, src[2] + c) for a in (-1, 0, 2) for b in (-2, 0, 1) for c in (-1, 0, 1)]
+    far = [(n[0], n[1], z), (n[0], 0, 0), (0, n[1], z), (n[0] // 2, n[1] // 2, 0), (n[0] - 4, 3, 2),
+           (3, n[1] - 3, z - 2), (n[0] // 3, n[1] // 2 + 7, z)]
+    nodes = near + far
+    me = gpu_mesh(nmgb, p, precision)
+    h = me.h_eff(torch.from_numpy(m).cuda(), inp.DEMAG, 0.0)
+    got = _gather(h, nodes)
+    me.close()
+    del h
+    ref = sampled.demag_at_nodes(n, p.dx, p.Ms, m, nodes)
+    assert rel_l2(got, ref) < TOL[precision]
+    assert np.abs(got - ref).max() <= TOL[precision] * np.abs(ref).max()
