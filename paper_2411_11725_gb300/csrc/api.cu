@@ -256,8 +256,8 @@ int create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int 
     ALLOC(M->n_bad_d, sizeof(unsigned long long));
 #undef ALLOC
     {
-        const int er = precision == NM_F64 ? demag_encode_ymap<double>(g, M->S, &M->ymap_inv)
-                                           : demag_encode_ymap<float>(g, M->S, &M->ymap_inv);
+        const int er = precision == NM_F64 ? demag_encode_ymap<double>(g, M->S, &M->ymap)
+                                           : demag_encode_ymap<float>(g, M->S, &M->ymap);
         if (er != 0) {
             release(M);
             return fail(NM_ERR_CUDA, "TMA descriptor of the inverse y pass refused (code %d)", er);

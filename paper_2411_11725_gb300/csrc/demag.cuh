@@ -39,9 +39,9 @@ struct DemagBufs {
     T Ms0;
     const StepCtl *ctl;        // when set, passes do nothing once ctl->done (finished integrations)
     Marker mark;               // profiling hook
-    // TMA descriptor of the inverse y pass over S (host copy, passed to the kernel by value; built
-    // once per mesh by demag_encode_ymap)
-    const CUtensorMap *ymap_inv = nullptr;
+    // TMA descriptor of a y-pass tile over S, all P2 rows (the inverse pass's load and the forward pass's
+    // store; host copy, passed to the kernels by value; built once per mesh by demag_encode_ymap)
+    const CUtensorMap *ymap = nullptr;
     int *wait_err = nullptr;   // device status word set to NM_ERR_TIMEOUT when a bounded wait runs out
 };
 
@@ -59,7 +59,7 @@ struct DemagPlan {
     bool z_reg;                // FP32, P3 <= 64: the register z convolution (two threads per line)
     int yc_G, yc_threads;
     size_t yc_smem;
-    size_t yi_smem;            // inverse y pass (TMA tile: alignment slack and barrier)
+    size_t yi_smem;            // y passes with a TMA tile (alignment slack and barrier)
 };
 template <typename T>
 DemagPlan demag_plan(const Geom &g);
@@ -73,10 +73,10 @@ void demag_forward(const Geom &g, const DemagBufs<T> &b, const T *y, T *MsH, cud
 template <typename T>
 void demag_cells(const Geom &g, const DemagBufs<T> &b, const T *M, T *H, cudaStream_t st);
 
-// TMA descriptor of the inverse y pass over the spectrum buffer S (host work only; no device access).
+// TMA descriptor of a y-pass tile over the spectrum buffer S (host work only; no device access).
 // Returns 0, or a non-zero code when the driver's encoder is unavailable or refuses the shape.
 template <typename T>
-int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *inv);
+int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *map);
 
 // Raise the dynamic shared-memory limit of every demag kernel once (outside any graph capture).
 void demag_init_attributes();

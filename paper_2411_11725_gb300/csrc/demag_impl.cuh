@@ -8,7 +8,8 @@
 // the FFT stages is resolved at compile time.  The x passes read their input in the first FFT stage
 // straight from global memory (the zero padding is never read); the forward y pass and the z passes
 // stage their strided tiles in shared memory with cp.async (all copies of a tile in flight at once), the
-// inverse y pass with one TMA tensor copy per tile.  Every pass writes its
+// inverse y pass with one TMA tensor copy per tile, and the forward y pass writes its tile back with one
+// TMA tensor store.  Every pass writes its
 // output from the last FFT stage straight to global memory, and only the part that later passes read.
 //
 // Templates only: demag_f32.cu and demag_f64.cu instantiate them (two translation units, compiled in
@@ -362,6 +363,29 @@ __device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap *tm,
         : "memory");
 }
 
+// TMA tile store from shared memory (bulk group); the writes of the threads that filled the tile must
+// be made visible to the copy first (fence_proxy_async by every writer, then a barrier)
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *tm, int c0, int c1, int c2, unsigned src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                     (unsigned long long)tm),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_store_4d(const CUtensorMap *tm, int c0, int c1, int c2, int c3, unsigned src)
+{
+    asm volatile("cp.async.bulk.tensor.4d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4}], [%5];\n" ::"l"(
+                     (unsigned long long)tm),
+                 "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(src)
+                 : "memory");
+}
+// commit the issued stores and wait until they have read their shared-memory source
+__device__ __forceinline__ void tma_store_commit_wait_read()
+{
+    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+
 // Bytes of the inverse y pass's TMA tile copy (all P2 rows): groups of 8 rows plus the zero-filled
 // padding row when the tile pads its rows (LFP = 3), plain rows otherwise (the box of demag_encode_ymap)
 template <typename T, int LG>
@@ -375,17 +399,23 @@ __host__ __device__ constexpr unsigned y_tile_bytes()
 // Forward reads y < N2 (zero padding above) and writes all P2; inverse reads all P2, writes y < N2.
 // Shared layout: row y at buf + lfpad(y) * G (lines = columns, fastest; padded rows for narrow tiles).
 //
-// Forward y pass: the N2 input rows of the tile staged with cp.async (all copies in flight at once).
-// (A TMA copy of the same box was measured slower here: 0.693 against 0.674 ms at 1024x1024x32.)
+// Forward y pass: the N2 input rows of the tile are staged with cp.async (all copies in flight at once;
+// a TMA copy of the same rows measured slower here, 0.693 against 0.674 ms at 1024x1024x32).  The last
+// stage writes the P2 outputs back into the tile, and one TMA store writes the whole tile (the box of
+// the inverse pass's load, descriptor tm: its ninth row per group of 8 lies outside the tensor and is
+// not written): 0.588 against 0.674 ms with the last stage storing to global memory itself.
 template <typename T, int LG>
-__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y_fwd(Geom g, DemagBufs<T> b)
+__global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>)
+    k_y_fwd(Geom g, DemagBufs<T> b, const __grid_constant__ CUtensorMap tm)
 {
     if (b.ctl && b.ctl->done) return;
     constexpr int P2 = 1 << LG, G = YTile<T, LG>::G, LFP = YTile<T, LG>::LFP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw);
-    Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
-    const int nin = g.N2, nout = P2;
+    // the tile at the first 128-byte boundary of the dynamic buffer (the source of the TMA store)
+    const unsigned pad = (128u - (smem_u32(smem_raw) & 127u)) & 127u;
+    Cx<T> *buf = reinterpret_cast<Cx<T> *>(smem_raw + pad);
+    const Cx<T> *base = b.S + (long)blockIdx.y * P2 * g.Xp + blockIdx.x * G;
+    const int nin = g.N2;
     const int Xp = g.Xp;
     constexpr int rowb = G * (int)sizeof(Cx<T>);
     constexpr int cb = rowb >= 16 ? 16 : rowb;
@@ -396,9 +426,16 @@ __global__ void __launch_bounds__(kMaxThreads<T, LG>, kMinBlocks<T, LG>) k_y_fwd
     }
     cpa_wait_all();
     __syncthreads();
-    auto dst = [&](int l, int i, Cx<T> v) { base[i * Xp + l] = v; };
-    f3::fft<T, LG, -1, true, true, false, kYEpt<T, LG>, G, LFP>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, nout,
-                                                                f3::NoFn<T>(), dst);
+    f3::fft<T, LG, -1, true, true, true, kYEpt<T, LG>, G, LFP>(buf, G, FastDiv(1u), b.tw, g.twlg, nin, P2,
+                                                               f3::NoFn<T>(), f3::NoFn<T>());
+    fence_proxy_async();  // (the transform ends with a barrier; this one orders the copy after every fence)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int x0 = 2 * G * blockIdx.x;  // real elements: a multiple of 2G, i.e. of 16 bytes
+        if constexpr (LFP > 0) tma_store_4d(&tm, x0, 0, 0, blockIdx.y, smem_u32(buf));
+        else tma_store_3d(&tm, x0, 0, blockIdx.y, smem_u32(buf));
+        tma_store_commit_wait_read();
+    }
 }
 
 // Inverse y pass: the whole P2-row tile arrives by one TMA copy (descriptor tm, built by
@@ -952,12 +989,13 @@ DemagPlan demag_plan(const Geom &g)
 }
 
 // ---------------------------------------------------------------------------------------------
-// TMA descriptor of the inverse y pass over S = [3][N3][P2][Xp] complex: every (component, z) plane
-// holds P2 rows of Xp complex values (rows of Xp * sizeof(Cx<T>) bytes, a multiple of 128).  Dimensions
-// in real elements, innermost first: the 2 Xp reals of a row, then (LFP = 3) the row within its group of
-// 8 and the group, or (LFP = 0) the row, then the 3 N3 planes.  The box is the 2G reals of a block's G kx
-// columns by all P2 rows of one plane: P2 / 8 groups of 9 rows (the ninth outside the tensor and
-// zero-filled: the padding row of the shared layout), or P2 plain rows.
+// TMA descriptor of a y-pass tile (the inverse pass's load, the forward pass's store) over
+// S = [3][N3][P2][Xp] complex: every (component, z) plane holds P2 rows of Xp complex values (rows of
+// Xp * sizeof(Cx<T>) bytes, a multiple of 128).  Dimensions in real elements, innermost first: the 2 Xp
+// reals of a row, then (LFP = 3) the row within its group of 8 and the group, or (LFP = 0) the row, then
+// the 3 N3 planes.  The box is the 2G reals of a block's G kx columns by all P2 rows of one plane: P2 / 8
+// groups of 9 rows (the ninth outside the tensor, zero-filled by a load and skipped by a store: the
+// padding row of the shared layout), or P2 plain rows.
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                    const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -975,9 +1013,9 @@ static EncodeTiledFn encode_tiled_fn()
 }
 
 template <typename T>
-int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *inv)
+int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *map)
 {
-    memset(inv, 0, sizeof(CUtensorMap));
+    memset(map, 0, sizeof(CUtensorMap));
     if (g.N3 <= 1 || g.P2 <= 1) return 0;  // no y passes
     const EncodeTiledFn enc = encode_tiled_fn();
     if (!enc) return -1;
@@ -993,13 +1031,13 @@ int demag_encode_ymap(const Geom &g, void *S, CUtensorMap *inv)
         const cuuint64_t dims[4] = {(cuuint64_t)2 * g.Xp, 8, (cuuint64_t)g.P2 / 8, (cuuint64_t)3 * g.N3};
         const cuuint64_t strides[3] = {rowb, 8 * rowb, (cuuint64_t)g.P2 * rowb};
         const cuuint32_t box[4] = {(cuuint32_t)(2 * p.y_G), 9, (cuuint32_t)(g.P2 / 8), 1};
-        r = enc(inv, dt, 4, S, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        r = enc(map, dt, 4, S, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         const cuuint64_t dims[3] = {(cuuint64_t)2 * g.Xp, (cuuint64_t)g.P2, (cuuint64_t)3 * g.N3};
         const cuuint64_t strides[2] = {rowb, (cuuint64_t)g.P2 * rowb};
         const cuuint32_t box[3] = {(cuuint32_t)(2 * p.y_G), (cuuint32_t)g.P2, 1};
-        r = enc(inv, dt, 3, S, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        r = enc(map, dt, 3, S, dims, strides, box, ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     return r == CUDA_SUCCESS ? 0 : (int)r;
@@ -1011,7 +1049,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
     const DemagPlan p = demag_plan<T>(g);
     if (!p.ok) return;
     // (create_mesh refuses shapes without a plan or, where there are y passes, without their descriptors)
-    if (g.N3 > 1 && g.P2 > 1 && !b.ymap_inv) return;
+    if (g.N3 > 1 && g.P2 > 1 && !b.ymap) return;
     const int nlines = 3 * g.N2 * g.N3;
     if (g.P1 == 1) {
         k_x_fwd1<T, CELL><<<div_up(nlines, 256), 256, 0, st>>>(g, b, in);
@@ -1026,7 +1064,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
                 constexpr int LG = decltype(c)::value;
-                k_y_fwd<T, LG><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.y_smem, st>>>(g, b);
+                k_y_fwd<T, LG><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.yi_smem, st>>>(g, b, *b.ymap);
             });
             b.mark("demag_y_fwd");
         }
@@ -1048,7 +1086,7 @@ static void run_pipeline(const Geom &g, const DemagBufs<T> &b, const T *in, T *o
         if (g.P2 > 1) {
             f3::lg_dispatch<1, 11>(g.lgP2, [&](auto c) {
                 constexpr int LG = decltype(c)::value;
-                k_y_inv<T, LG><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.yi_smem, st>>>(g, b, *b.ymap_inv);
+                k_y_inv<T, LG><<<dim3(g.Xp / p.y_G, 3 * g.N3), p.y_threads, p.yi_smem, st>>>(g, b, *b.ymap);
             });
             b.mark("demag_y_inv");
         }

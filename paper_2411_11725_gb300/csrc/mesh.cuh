@@ -109,7 +109,7 @@ struct nm_mesh_s {
     size_t prof_n = 0;
     unsigned long long *n_bad_d = nullptr;  // nodes with non-finite values met by nm_set_state (device)
     int err_f64_terms = 0;  // FP32 meshes: per-node error-norm terms in FP64 (nm_set_error_norm)
-    CUtensorMap ymap_inv;   // TMA descriptor of the inverse y pass over S
+    CUtensorMap ymap;       // TMA descriptor of a y-pass tile over S (all P2 rows)
 };
 
 
@@ -270,7 +270,7 @@ inline DemagBufs<T> demag_bufs(nm_mesh M)
     b.Ms0 = (T)M->Ms0;
     b.ctl = nullptr;
     b.mark = marker(M);
-    b.ymap_inv = &M->ymap_inv;
+    b.ymap = &M->ymap;
     b.wait_err = &M->ctl->status;
     return b;
 }
