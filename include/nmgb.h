@@ -83,8 +83,11 @@ typedef struct nm_mesh_s *nm_mesh;
  * working on the CUDA stream `cuda_stream` (a cudaStream_t; NULL = legacy default stream).
  * Supported sizes: 1 <= n1, n2 <= 1024 and 1 <= n3 <= 64 (padded transform lengths up to 2048 along x
  * and y and 128 along z); nm_footprint_bytes gives the device memory a size takes.
- * Allocates every device workspace the mesh needs.  Errors: NM_ERR_ARG (n_k < 1, a size beyond the
- * supported range, dx_k <= 0, bad precision, out == NULL), NM_ERR_OOM, NM_ERR_CUDA. */
+ * Allocates every device workspace the mesh needs, and encodes on the host the TMA descriptor that the
+ * y passes of the demag transform use for their tiles of the spectrum buffer.  Errors: NM_ERR_ARG
+ * (n_k < 1, a size beyond the supported range, dx_k <= 0, bad precision, out == NULL), NM_ERR_OOM,
+ * NM_ERR_CUDA (a CUDA call failed, or the driver's descriptor encoder is unavailable or refused the
+ * shape). */
 int nm_create_mesh(int n1, int n2, int n3, double dx1, double dx2, double dx3, int precision,
                    void *cuda_stream, nm_mesh *out);
 
@@ -170,7 +173,8 @@ int nm_set_dmi(nm_mesh mesh, const double *D, double D0);
 /* One integrator step on the resident state.  NM_RK4 uses *dt as the fixed step; NM_DP54 attempts
  * *dt and on return *dt holds the proposed next step, *accepted tells whether the attempt was taken
  * (error norm <= 1 with tolerances rtol, atol).  *t is advanced on acceptance.  Synchronises.
- * Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_STEP_UNDERFLOW, NM_ERR_CUDA. */
+ * Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_STEP_UNDERFLOW, NM_ERR_TIMEOUT (a demag pass's bounded wait
+ * for its TMA tile copy ran out: not expected on a working GPU), NM_ERR_CUDA. */
 int nm_llg_step(nm_mesh mesh, int method, double *t, double *dt, double rtol, double atol, int *accepted);
 
 /* n_steps step attempts with no host round trip in between (step control runs on the device; the
@@ -192,7 +196,7 @@ int nm_get_counters(nm_mesh mesh, long *n_accepted, long *n_rejected, double *la
  * mean of m (weights: lumped nodal volume) is written to samples_out[k*3 + j] (host FP64 array of
  * max_samples x 3) for k = 0 .. while t0 + k sample_dt <= t_end (k = 0 is the initial state).
  * n_accepted / n_rejected may be NULL.  Errors: NM_ERR_ARG, NM_ERR_STATE, NM_ERR_STEP_UNDERFLOW,
- * NM_ERR_CUDA. */
+ * NM_ERR_TIMEOUT (as nm_llg_step), NM_ERR_CUDA. */
 int nm_run_until(nm_mesh mesh, double t_end, int method, double rtol, double atol, double dt0,
                  double sample_dt, double *samples_out, long max_samples, long *n_accepted,
                  long *n_rejected);
